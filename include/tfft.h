@@ -1,0 +1,199 @@
+/*
+ * tfft.h -- C ABI of a single-GPU (GB300, sm_103a) transpose-algorithm
+ * multidimensional FFT on a virtual Cartesian process grid.
+ *
+ * The method is that of Dalcin, Mortensen & Keyes, "Fast parallel
+ * multidimensional FFT using advanced MPI" (arXiv:1804.09536): a d-D DFT is
+ * computed one axis at a time as batched 1-D FFTs (Eq. fftn_forward), and
+ * between the partial transforms the array is redistributed so that the next
+ * axis is held in full by every process (Eq. general_gt, Eq. gt).  Here the
+ * processes are virtual: every "rank" is a block of one device buffer.
+ *
+ * Conventions used by every call below.
+ *
+ *  - Global shape N[0..d-1], C row-major (Sec. 3).  1 <= d <= 4.
+ *  - Process grid M[0..g-1], 0 <= g <= d-1 (Sec. 3.6); rank p has row-major
+ *    coordinates (p_0, ..., p_{g-1}) (Sec. 3.4).  g = 1 is the slab method
+ *    (Eqs. slab0-slab1), g = 2 the pencil method (Eqs. pencil0-pencil2).
+ *  - Stages s = 0 .. g.  In stage s grid direction i cuts axis i if
+ *    i < g - s, else axis i + 1.  Stage 0 is the input alignment; stage g
+ *    holds axis 0 in full and is the alignment of the forward output (axes are
+ *    not permuted, Sec. 3.3.1 end).  Each cut axis uses the balanced
+ *    block-contiguous decomposition of Eq. decompose / Alg. 1.
+ *  - Stage buffer: each rank's local array in C order, the ranks' arrays
+ *    concatenated in rank order.  tfft_plan_local_box() gives every rank's
+ *    block and offset.
+ *  - Elements are complex64 (interleaved float re, im; 8 bytes) except the
+ *    real stage-0 buffer of a real-to-complex plan (float32).  The complex
+ *    global shape of a real-to-complex plan is N[0..d-2], N[d-1]/2 + 1
+ *    (footnote to Eq. multifft).
+ *  - Sign: TFFT_FORWARD = -1 (exp(-i k x)), TFFT_BACKWARD = +1, as in the
+ *    appendix listings.  Normalisation (Eqs. 1-2, Eq. multifft): the forward
+ *    transform carries 1/prod(N), the backward none; TFFT_NORM_BACKWARD moves
+ *    the factor to the backward transform.  The factor is formed in double
+ *    precision and applied once, in the last pass, as a float.
+ *
+ * Memory ownership: the library never allocates device memory.  Every device
+ * buffer (plan state, inputs, outputs, workspace) is allocated and freed by
+ * the caller; the plan itself is a host object.  Every device pointer must be
+ * 16-byte aligned.  Calls are asynchronous on the given stream (a
+ * cudaStream_t passed as void*; NULL is the legacy default stream) and do not
+ * synchronise, except tfft_plan_bind(), which is a set-up call and returns
+ * after its copies are complete.
+ *
+ * Errors: every call returns a tfft_status.  Arguments are validated before
+ * anything is launched; on an error nothing is launched and
+ * tfft_last_error() returns a message (per thread).  A CUDA launch error is
+ * reported as TFFT_ECUDA; errors of kernels already running surface on a
+ * later call or on the caller's synchronisation.  No call traps the device.
+ */
+#ifndef TFFT_H
+#define TFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TFFT_MAX_DIMS 4
+#define TFFT_MAX_GRID_DIMS 3
+
+typedef struct tfft_plan_s *tfft_plan;
+
+enum { TFFT_FORWARD = -1, TFFT_BACKWARD = +1 };
+enum { TFFT_C2C = 0, TFFT_R2C = 1 };
+enum { TFFT_FP32 = 0 };
+/* plan flags */
+enum { TFFT_NORM_FORWARD = 0, TFFT_NORM_BACKWARD = 4 };
+/* execution modes of tfft_execute */
+enum {
+  TFFT_MODE_FUSED = 0,   /* redistributions fused into the FFT passes' loads/stores */
+  TFFT_MODE_UNFUSED = 1, /* FFT passes + one subarray exchange kernel per redistribution */
+  TFFT_MODE_PACKED = 2   /* FFT passes + pack (local transpose) -> all-to-all copy -> unpack */
+};
+
+typedef enum {
+  TFFT_OK = 0,
+  TFFT_EINVAL = 1,       /* bad argument (shape, grid, axis, stage, sign, pointer) */
+  TFFT_EUNSUPPORTED = 2, /* valid request this build does not implement (e.g. a prime length) */
+  TFFT_EALIGN = 3,       /* a device pointer is not 16-byte aligned */
+  TFFT_EWORKSPACE = 4,   /* workspace missing or too small */
+  TFFT_ECUDA = 5,        /* a CUDA runtime call failed */
+  TFFT_ESTATE = 6        /* plan not bound to a device state buffer */
+} tfft_status;
+
+/* Human-readable name of a status code (static string). */
+const char *tfft_status_string(int status);
+/* Detail of the last error on the calling thread (static per-thread buffer). */
+const char *tfft_last_error(void);
+/* ABI version, major * 100 + minor. */
+int tfft_version(void);
+
+/*
+ * Balanced block-contiguous decomposition, Eq. decompose / Alg. 1 (Sec. 3.1):
+ * part p of N elements split in M parts has n = q + (r > p) elements starting
+ * at s = q p + min(r, p), q = N / M, r = N mod M.  Requires N >= 0, M > 0,
+ * 0 <= p < M; n and s must be non-NULL host pointers.
+ */
+int tfft_decompose(int64_t N, int64_t M, int64_t p, int64_t *n, int64_t *s);
+
+/*
+ * Create a plan for a d-D transform of global shape shape[0..ndims-1] on a
+ * grid_ndims-D virtual process grid grid[0..grid_ndims-1] (Sec. 3.4; the grid
+ * is taken as given, no dims-create balancing).  kind: TFFT_C2C or TFFT_R2C
+ * (real input, Hermitian half on the last axis; N[d-1] even).  precision:
+ * TFFT_FP32.  flags: TFFT_NORM_FORWARD or TFFT_NORM_BACKWARD.
+ * Transforms need every length to factor into 2, 3 and 5 and be <= 4096;
+ * a plan with other lengths is still created and redistributes, but its
+ * tfft_execute() and tfft_partial() return TFFT_EUNSUPPORTED.
+ * The plan is a host object; destroy it with tfft_plan_destroy().
+ */
+int tfft_plan_create(tfft_plan *plan, int ndims, const int64_t *shape, int grid_ndims,
+                     const int *grid, int kind, int precision, int flags);
+int tfft_plan_destroy(tfft_plan plan);
+
+/* Number of stages (grid_ndims + 1) and of virtual ranks (product of the grid). */
+int tfft_plan_num_stages(tfft_plan plan, int *nstages);
+int tfft_plan_num_ranks(tfft_plan plan, int *nranks);
+/* Axis newly held in full by a stage: grid_ndims - stage (Sec. 3.3-3.6). */
+int tfft_plan_stage_axis(tfft_plan plan, int stage, int *axis);
+/* Elements of a whole stage buffer.  real != 0 asks for the real stage-0
+   buffer of an R2C plan (stage must be 0). */
+int tfft_plan_stage_elems(tfft_plan plan, int stage, int real, int64_t *elems);
+/* Block of one rank in a stage: start[d], size[d] (global index space) and the
+   element offset of its local array in the stage buffer.  Host pointers. */
+int tfft_plan_local_box(tfft_plan plan, int stage, int real, int rank, int64_t *start,
+                        int64_t *size, int64_t *offset);
+
+/*
+ * Plan state: tables the kernels read (rank offsets, twiddle factors,
+ * column blocks, subarray boxes).  The caller allocates tfft_plan_state_bytes()
+ * bytes of device memory and passes it to tfft_plan_bind(), which uploads the
+ * tables and generates the twiddle factors on the device in double precision
+ * (then rounds them to float).  The state must stay allocated and unmodified
+ * while the plan is used; bind again after moving it.
+ */
+int tfft_plan_state_bytes(tfft_plan plan, size_t *bytes);
+int tfft_plan_bind(tfft_plan plan, void *d_state, size_t bytes, void *stream);
+
+/*
+ * Workspace of tfft_execute() in a mode, in bytes.  TFFT_MODE_FUSED: 0 for
+ * C2C (the input buffer is then overwritten) -- pass one stage buffer's worth
+ * to keep the input; R2C always needs one complex stage buffer.  UNFUSED and
+ * PACKED: two complex stage buffers.
+ */
+int tfft_plan_workspace_bytes(tfft_plan plan, int mode, int keep_input, size_t *bytes);
+
+/*
+ * Global redistribution of Alg. 3 / Eq. gt between two adjacent stages:
+ * from the stage that holds axis_v in full (input, aligned in v) to the stage
+ * that holds axis_w in full (output, aligned in w), within the one-dimensional
+ * subgroups of the grid direction that moves.  All subgroups exchange
+ * concurrently in one launch; every (sender, receiver) pair copies one
+ * subarray box straight from the input to the output (the all-to-all-w of
+ * subarray types).  Bit-exact copy.  in and out are stage buffers of the
+ * plan's complex shape and must not overlap.
+ */
+int tfft_redistribute(tfft_plan plan, int axis_v, int axis_w, const void *in, void *out,
+                      void *stream);
+
+/*
+ * Partial transform F_axis (Sec. 2, the appendix's sequential routine): 1-D
+ * DFT of sign `sign` along `axis` of every rank's local array in `stage`, in
+ * place.  axis must be held in full in that stage.  The forward direction
+ * includes 1/N_axis (Eq. multifft), the backward none.
+ */
+int tfft_partial(tfft_plan plan, int stage, int axis, int sign, void *inout, void *stream);
+
+/*
+ * Whole transform.  sign TFFT_FORWARD: in = stage-0 buffer (float32 for R2C),
+ * out = stage-g buffer (Eqs. pencil0-pencil2 and their d-D form).
+ * TFFT_BACKWARD: in = stage-g buffer, out = stage-0 buffer (the forward steps
+ * reversed, App. A).  mode selects the fused path or one of the two
+ * comparison paths; all three give the same result.  work / work_bytes: see
+ * tfft_plan_workspace_bytes().  When work is NULL in TFFT_MODE_FUSED C2C the
+ * input buffer is used as scratch; a complex-to-real backward always
+ * overwrites its input.  in and out must not overlap.
+ */
+int tfft_execute(tfft_plan plan, int sign, int mode, const void *in, void *out, void *work,
+                 size_t work_bytes, void *stream);
+
+/* Number of kernel launches tfft_execute() makes in a mode and direction. */
+int tfft_plan_num_launches(tfft_plan plan, int sign, int mode, int *nlaunches);
+
+/*
+ * Timing hook: record caller-created CUDA events (cudaEvent_t as void*) on
+ * the execution stream around every launch of the following tfft_execute()
+ * calls: events[k] before launch k and events[n] after the last, n =
+ * tfft_plan_num_launches().  count must be >= n + 1.  count = 0 removes the
+ * hook.  The events stay owned by the caller.
+ */
+int tfft_plan_set_launch_events(tfft_plan plan, void *const *events, int count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFFT_H */

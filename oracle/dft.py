@@ -202,3 +202,29 @@ def distributed_irfft_backward(buf_c, shape, grid, exchange=redistribute.exchang
         full = hermitian_extend_last(loc, shape[-1])
         out[off:off + math.prod(sz)] = partial_dft(full, d - 1, BACKWARD).real.reshape(-1)
     return out
+
+
+def forward_at(x: np.ndarray, ks, chunk: int = 32) -> np.ndarray:
+    """Selected outputs of the d-D forward transform (Eq. multifft), one index at a time.
+
+    X[k] = sum_{j_0} (w_0^{k_0 j_0} / N_0) ... sum_{j_{d-1}} (w_{d-1}^{k_{d-1} j_{d-1}} / N_{d-1}) x[j]
+    evaluated by contracting the last axis first, ``chunk`` slices of axis 0 at a
+    time so that large arrays (e.g. 512^3) need little extra memory.
+    """
+    x = np.asarray(x)
+    shape = x.shape
+    d = x.ndim
+    out = np.empty(len(ks), dtype=np.complex128)
+    for n, k in enumerate(ks):
+        vecs = []
+        for m in range(d):
+            j = np.arange(shape[m], dtype=np.int64)
+            vecs.append(np.exp(-2j * np.pi * ((k[m] * j) % shape[m]) / shape[m]) / shape[m])
+        acc = np.zeros((), dtype=np.complex128)
+        for a in range(0, shape[0], chunk):
+            blk = x[a:a + chunk].astype(np.complex128)
+            for m in range(d - 1, 0, -1):
+                blk = blk @ vecs[m]
+            acc = acc + blk @ vecs[0][a:a + chunk]
+        out[n] = acc
+    return out

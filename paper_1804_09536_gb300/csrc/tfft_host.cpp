@@ -1,0 +1,927 @@
+// Host side of the C ABI (include/tfft.h): plan construction on the virtual
+// process grid, state image, pass lists and launches.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tfft.h"
+#include "tfft_internal.h"
+
+using namespace tfft;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return TFFT_ECUDA;
+}
+
+// Eq. decompose / Alg. 1.
+void decompose(int64_t N, int64_t M, int64_t p, int64_t& n, int64_t& s) {
+  const int64_t q = N / M, r = N % M;
+  n = q + (r > p ? 1 : 0);
+  s = q * p + std::min(r, p);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct LayoutH {
+  int d = 0;
+  int64_t N[MAXD] = {0, 0, 0, 0};
+  int owner[MAXD] = {-1, -1, -1, -1};
+  int nranks = 0;
+  std::vector<int64_t> start, size, offset;  // nranks * d, nranks * d, nranks
+  int64_t total = 0;
+  size_t state_off = 0;  // rank offset table in the state image (bytes)
+};
+
+enum StepKind { S_CONTIG, S_STRIDED, S_BOX };
+enum BufId { BUF_IN, BUF_OUT, BUF_W0, BUF_W1 };
+
+struct Step {
+  StepKind kind;
+  int src = BUF_IN, dst = BUF_OUT;
+  bool inplace_ok = true;
+  // FFT passes
+  int axis = 0, lin = 0, lout = 0, L = 1, W = 16;
+  int64_t nlines = 0;
+  size_t cb_off = 0;
+  int64_t ncb = 0;
+  int sign = -1;
+  bool scaled = false;
+  double scale_value = 1.0;
+  // box copies
+  size_t box_off = 0;
+  int nboxes = 0;
+  int64_t max_rows = 0;
+  int vec2 = 0;
+};
+
+struct ExchangeBoxes {  // one adjacent-stage exchange
+  std::vector<BoxDesc> direct, pack, xchg, unpack;
+  bool pack_identity = false, unpack_identity = false;
+};
+
+}  // namespace
+
+struct tfft_plan_s {
+  int d = 0, g = 0, kind = TFFT_C2C, precision = TFFT_FP32, flags = 0;
+  int64_t shape[MAXD] = {1, 1, 1, 1};
+  int64_t cshape[MAXD] = {1, 1, 1, 1};
+  int grid[MAXG] = {1, 1, 1};
+  int64_t rstride[MAXG] = {0, 0, 0};
+  int nranks = 1;
+  int64_t nelems = 0;  // complex elements of every stage buffer
+  bool transformable = true;  // every axis length has an FFT plan
+  std::vector<LayoutH> st;
+  std::map<int, AxisPlan> aplan;   // contiguous-line passes
+  std::map<int, AxisPlan> aplan_s; // strided passes
+  std::map<int, size_t> tw_off;
+  std::map<std::tuple<int, int, int>, std::pair<size_t, int64_t>> colblocks;  // (lin,lout,W)
+  std::map<std::pair<int, int>, ExchangeBoxes> xboxes;                       // (from,to)
+  std::map<std::pair<int, int>, std::vector<size_t>> xbox_off;  // direct, pack, xchg, unpack
+  std::map<std::pair<int, int>, std::vector<Step>> steps;        // (sign, mode)
+  std::vector<uint8_t> image;
+  size_t state_bytes = 0;
+  char* d_state = nullptr;
+  std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+size_t image_add(tfft_plan p, const void* data, size_t bytes) {
+  const size_t off = align_up(p->image.size(), 256);
+  p->image.resize(off + bytes, 0);
+  if (data && bytes) std::memcpy(p->image.data() + off, data, bytes);
+  return off;
+}
+
+void build_layout(tfft_plan p, const int64_t* shape, int stage, LayoutH& L) {
+  L.d = p->d;
+  for (int m = 0; m < MAXD; ++m) {
+    L.N[m] = m < p->d ? shape[m] : 1;
+    L.owner[m] = -1;
+  }
+  for (int i = 0; i < p->g; ++i) {
+    const int axis = (i < p->g - stage) ? i : i + 1;
+    L.owner[axis] = i;
+  }
+  L.nranks = p->nranks;
+  L.start.assign((size_t)p->nranks * p->d, 0);
+  L.size.assign((size_t)p->nranks * p->d, 0);
+  L.offset.assign(p->nranks, 0);
+  int64_t off = 0;
+  for (int r = 0; r < p->nranks; ++r) {
+    int64_t coords[MAXG] = {0, 0, 0};
+    int64_t rr = r;
+    for (int i = p->g - 1; i >= 0; --i) {
+      coords[i] = rr % p->grid[i];
+      rr /= p->grid[i];
+    }
+    int64_t cnt = 1;
+    for (int m = 0; m < p->d; ++m) {
+      int64_t n = L.N[m], s = 0;
+      if (L.owner[m] >= 0) decompose(L.N[m], p->grid[L.owner[m]], coords[L.owner[m]], n, s);
+      L.start[(size_t)r * p->d + m] = s;
+      L.size[(size_t)r * p->d + m] = n;
+      cnt *= n;
+    }
+    L.offset[r] = off;
+    off += cnt;
+  }
+  L.total = off;
+}
+
+DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
+  DevLayout D;
+  D.d = L.d;
+  for (int m = 0; m < MAXD; ++m) {
+    D.N[m] = L.N[m];
+    D.Mx[m] = L.owner[m] >= 0 ? p->grid[L.owner[m]] : 1;
+    D.rs[m] = L.owner[m] >= 0 ? p->rstride[L.owner[m]] : 0;
+  }
+  D.offset = reinterpret_cast<const int64_t*>(p->d_state + L.state_off);
+  return D;
+}
+
+// 1-D FFT plan: radices from {16, 8, 5, 4, 3, 2} that all divide E, fewest
+// stages first, then the largest smallest radix, then E preference.
+// `strided`: the line is one column of a W-wide tile of at most 512 threads,
+// so plans with at most 32 threads per line (W >= 16 columns) are preferred.
+bool make_axis_plan(int L, bool strided, AxisPlan& best) {
+  if (L == 1) {
+    best = AxisPlan{1, 1, 1, 0, 0, {}};
+    return true;
+  }
+  static const int Es[] = {8, 16, 4, 12, 20, 24, 10, 6, 15, 5, 3, 2};
+  static const int Rs[] = {16, 8, 5, 4, 3, 2};
+  bool found = false;
+  double best_cost = 1e30;
+  for (int E : Es) {
+    if (L % E != 0 || !kernel_supports_E(E)) continue;
+    if (L / E > 1024) continue;
+    // enumerate factorizations by depth-first search over non-increasing radices
+    std::vector<int> cur, bestv;
+    double bc = 1e30;
+    std::vector<int> allowed;
+    for (int R : Rs)
+      if (E % R == 0) allowed.push_back(R);
+    std::function<void(int, int)> dfs = [&](int rem, int maxi) {
+      if ((int)cur.size() > MAXSTAGES) return;
+      if (rem == 1) {
+        int mn = *std::min_element(cur.begin(), cur.end());
+        double c = cur.size() * 10.0 - mn * 0.1;
+        if (c < bc) {
+          bc = c;
+          bestv = cur;
+        }
+        return;
+      }
+      for (int k = maxi; k < (int)allowed.size(); ++k) {
+        const int R = allowed[k];
+        if (rem % R == 0) {
+          cur.push_back(R);
+          dfs(rem / R, k);
+          cur.pop_back();
+        }
+      }
+    };
+    dfs(L, 0);
+    if (bestv.empty()) continue;
+    double cost = bc + (E == 8 ? 0.0 : E == 16 ? 0.5 : E <= 16 ? 1.0 : 2.0);
+    if (strided && L / E > 64) cost += 3.0;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best.L = L;
+      best.E = E;
+      best.T = L / E;
+      best.nst = (int)bestv.size();
+      best.code = 0;
+      for (int s = 0; s < best.nst; ++s) {
+        best.radix[s] = bestv[s];
+        best.code |= (uint64_t)bestv[s] << (5 * s);
+      }
+      found = true;
+    }
+  }
+  return found;
+}
+
+int strided_width(const AxisPlan& ap) { return std::max(1, std::min(32, 512 / ap.T)); }
+
+// Column blocks along axis d-1 that lie inside one rank of both layouts.
+std::pair<size_t, int64_t> get_colblocks(tfft_plan p, int lin, int lout, int W) {
+  auto key = std::make_tuple(lin, lout, W);
+  auto it = p->colblocks.find(key);
+  if (it != p->colblocks.end()) return it->second;
+  const int last = p->d - 1;
+  const int64_t N = p->cshape[last];
+  std::vector<int64_t> cuts = {0, N};
+  for (int li : {lin, lout}) {
+    const LayoutH& L = p->st[li];
+    if (L.owner[last] >= 0) {
+      const int M = p->grid[L.owner[last]];
+      for (int q = 0; q < M; ++q) {
+        int64_t n, s;
+        decompose(N, M, q, n, s);
+        cuts.push_back(s);
+      }
+    }
+  }
+  std::sort(cuts.begin(), cuts.end());
+  cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+  std::vector<int2> blocks;
+  for (size_t k = 0; k + 1 < cuts.size(); ++k)
+    for (int64_t c = cuts[k]; c < cuts[k + 1]; c += W)
+      blocks.push_back(make_int2((int)c, (int)std::min<int64_t>(W, cuts[k + 1] - c)));
+  const size_t off = image_add(p, blocks.data(), blocks.size() * sizeof(int2));
+  auto v = std::make_pair(off, (int64_t)blocks.size());
+  p->colblocks[key] = v;
+  return v;
+}
+
+BoxDesc make_box(int d, const int64_t* ext, int64_t src, const int64_t* ss, int64_t dst,
+                 const int64_t* ds) {
+  BoxDesc b;
+  b.src = src;
+  b.dst = dst;
+  const int pad = MAXD - d;
+  for (int m = 0; m < MAXD; ++m) {
+    if (m < pad) {
+      b.ext[m] = 1;
+      b.ss[m] = 0;
+      b.ds[m] = 0;
+    } else {
+      b.ext[m] = ext[m - pad];
+      b.ss[m] = ss[m - pad];
+      b.ds[m] = ds[m - pad];
+    }
+  }
+  return b;
+}
+
+void row_major_strides(int d, const int64_t* ext, int64_t* st) {
+  int64_t s = 1;
+  for (int m = d - 1; m >= 0; --m) {
+    st[m] = s;
+    s *= ext[m];
+  }
+}
+
+// A flat copy of n contiguous elements as boxes of (n / 1024, 1024) rows plus a tail.
+void add_flat(std::vector<BoxDesc>& out, int64_t src, int64_t dst, int64_t n) {
+  const int64_t C = 1024;
+  if (n <= 0) return;
+  const int64_t rows = n / C, tail = n - rows * C;
+  if (rows > 0) {
+    const int64_t ext[2] = {rows, C}, st[2] = {C, 1};
+    out.push_back(make_box(2, ext, src, st, dst, st));
+  }
+  if (tail > 0) {
+    const int64_t ext[1] = {tail}, st[1] = {1};
+    out.push_back(make_box(1, ext, src + rows * C, st, dst + rows * C, st));
+  }
+}
+
+bool box_contiguous(const BoxDesc& b, const int64_t* st) {
+  int64_t rm[MAXD];
+  row_major_strides(MAXD, b.ext, rm);
+  for (int m = 0; m < MAXD; ++m)
+    if (b.ext[m] > 1 && st[m] != rm[m]) return false;
+  return true;
+}
+
+// Boxes of the exchange between adjacent stages s_from -> s_to (Alg. 2 / Alg. 3).
+void build_exchange(tfft_plan p, int s_from, int s_to) {
+  const int d = p->d;
+  const int i = p->g - std::max(s_from, s_to);
+  const LayoutH& A = p->st[s_from];
+  const LayoutH& B = p->st[s_to];
+  int v = -1, w = -1;
+  for (int m = 0; m < d; ++m) {
+    if (B.owner[m] == i) v = m;  // A holds v whole, B cuts it
+    if (A.owner[m] == i) w = m;  // A cuts w, B holds it whole
+  }
+  const int M = p->grid[i];
+  ExchangeBoxes X;
+  X.pack_identity = true;
+  X.unpack_identity = true;
+  for (int a = 0; a < p->nranks; ++a) {
+    const int64_t pa = (a / p->rstride[i]) % M;  // a's coordinate in direction i
+    const int64_t* Aext = &A.size[(size_t)a * d];
+    int64_t Ast[MAXD];
+    row_major_strides(d, Aext, Ast);
+    int64_t packed = 0;
+    for (int q = 0; q < M; ++q) {
+      const int b = (int)(a + (q - pa) * p->rstride[i]);
+      const int64_t* Bext = &B.size[(size_t)b * d];
+      int64_t Bst[MAXD];
+      row_major_strides(d, Bext, Bst);
+      int64_t nq, sq, np_, sp;
+      decompose(p->cshape[v], M, q, nq, sq);
+      decompose(p->cshape[w], M, pa, np_, sp);
+      int64_t ext[MAXD];
+      int64_t cnt = 1;
+      for (int m = 0; m < d; ++m) {
+        ext[m] = (m == v) ? nq : Aext[m];
+        cnt *= ext[m];
+      }
+      if (cnt == 0) continue;
+      const int64_t src = A.offset[a] + sq * Ast[v];
+      const int64_t dst = B.offset[b] + sp * Bst[w];
+      X.direct.push_back(make_box(d, ext, src, Ast, dst, Bst));
+      // traditional: pack into rank a's send region, chunk q after chunks 0..q-1
+      int64_t cst[MAXD];
+      row_major_strides(d, ext, cst);
+      const int64_t psrc = src, pdst = A.offset[a] + packed;
+      BoxDesc pb = make_box(d, ext, psrc, Ast, pdst, cst);
+      X.pack.push_back(pb);
+      if (!(psrc == pdst && box_contiguous(pb, pb.ss))) X.pack_identity = false;
+      packed += cnt;
+    }
+  }
+  // all-to-all of contiguous chunks: rank b receives from p = 0..M-1 in order
+  for (int b = 0; b < p->nranks; ++b) {
+    const int64_t qb = (b / p->rstride[i]) % M;
+    const int64_t* Bext = &B.size[(size_t)b * d];
+    int64_t Bst[MAXD];
+    row_major_strides(d, Bext, Bst);
+    int64_t recv = 0;
+    for (int pp = 0; pp < M; ++pp) {
+      const int a = (int)(b + (pp - qb) * p->rstride[i]);
+      const int64_t* Aext = &A.size[(size_t)a * d];
+      // offset of chunk qb inside a's send region
+      int64_t before = 0;
+      for (int q = 0; q < qb; ++q) {
+        int64_t nq, sq;
+        decompose(p->cshape[v], M, q, nq, sq);
+        int64_t c = 1;
+        for (int m = 0; m < d; ++m) c *= (m == v) ? nq : Aext[m];
+        before += c;
+      }
+      int64_t nq, sq, np_, sp;
+      decompose(p->cshape[v], M, qb, nq, sq);
+      decompose(p->cshape[w], M, pp, np_, sp);
+      int64_t ext[MAXD];
+      int64_t cnt = 1;
+      for (int m = 0; m < d; ++m) {
+        ext[m] = (m == v) ? nq : Aext[m];
+        cnt *= ext[m];
+      }
+      if (cnt == 0) continue;
+      add_flat(X.xchg, A.offset[a] + before, B.offset[b] + recv, cnt);
+      int64_t cst[MAXD];
+      row_major_strides(d, ext, cst);
+      const int64_t usrc = B.offset[b] + recv, udst = B.offset[b] + sp * Bst[w];
+      BoxDesc ub = make_box(d, ext, usrc, cst, udst, Bst);
+      X.unpack.push_back(ub);
+      if (!(usrc == udst && box_contiguous(ub, ub.ds))) X.unpack_identity = false;
+      recv += cnt;
+    }
+  }
+  std::vector<size_t> offs;
+  for (auto* vec : {&X.direct, &X.pack, &X.xchg, &X.unpack})
+    offs.push_back(image_add(p, vec->data(), vec->size() * sizeof(BoxDesc)));
+  p->xboxes[{s_from, s_to}] = std::move(X);
+  p->xbox_off[{s_from, s_to}] = offs;
+}
+
+Step box_step(tfft_plan p, const std::vector<BoxDesc>& boxes, size_t off) {
+  Step s;
+  s.kind = S_BOX;
+  s.inplace_ok = false;
+  s.box_off = off;
+  s.nboxes = (int)boxes.size();
+  s.vec2 = 1;
+  for (const BoxDesc& b : boxes) {
+    s.max_rows = std::max<int64_t>(s.max_rows, b.ext[0] * b.ext[1] * b.ext[2]);
+    if ((b.src | b.dst | b.ext[3]) & 1) s.vec2 = 0;
+    for (int m = 0; m < MAXD; ++m)
+      if ((b.ss[m] | b.ds[m]) & 1) s.vec2 = 0;
+  }
+  (void)p;
+  return s;
+}
+
+Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
+  Step s;
+  s.sign = sign;
+  s.axis = axis;
+  s.lin = lin;
+  s.lout = lout;
+  s.L = (int)p->cshape[axis];
+  if (axis == p->d - 1) {
+    s.kind = S_CONTIG;
+    s.inplace_ok = true;
+    s.nlines = p->nelems / s.L;
+  } else {
+    s.kind = S_STRIDED;
+    s.inplace_ok = (lin == lout);
+    const AxisPlan& ap = p->aplan_s[s.L];
+    s.W = strided_width(ap);
+    auto cb = get_colblocks(p, lin, lout, s.W);
+    s.cb_off = cb.first;
+    s.ncb = cb.second;
+  }
+  return s;
+}
+
+void add_exchange_steps(tfft_plan p, std::vector<Step>& out, int from, int to, int mode) {
+  const ExchangeBoxes& X = p->xboxes[{from, to}];
+  const std::vector<size_t>& off = p->xbox_off[{from, to}];
+  if (mode == TFFT_MODE_UNFUSED) {
+    out.push_back(box_step(p, X.direct, off[0]));
+  } else {
+    if (!X.pack_identity) out.push_back(box_step(p, X.pack, off[1]));
+    out.push_back(box_step(p, X.xchg, off[2]));
+    if (!X.unpack_identity) out.push_back(box_step(p, X.unpack, off[3]));
+  }
+}
+
+// Logical step list of one direction and mode (buffers assigned later).
+std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
+  const int d = p->d, g = p->g;
+  std::vector<Step> v;
+  if (mode == TFFT_MODE_FUSED) {
+    if (sign == TFFT_FORWARD) {
+      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+      for (int a = d - 2; a >= 0; --a) v.push_back(fft_step(p, a, a == d - 2 ? 0 : g, g, sign));
+    } else {
+      for (int a = 0; a <= d - 2; ++a) v.push_back(fft_step(p, a, g, a == d - 2 ? 0 : g, sign));
+      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+    }
+  } else {
+    if (sign == TFFT_FORWARD) {
+      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+      for (int a = d - 2; a >= g; --a) v.push_back(fft_step(p, a, 0, 0, sign));
+      for (int s = 1; s <= g; ++s) {
+        add_exchange_steps(p, v, s - 1, s, mode);
+        v.push_back(fft_step(p, g - s, s, s, sign));
+      }
+    } else {
+      for (int s = g; s >= 1; --s) {
+        v.push_back(fft_step(p, g - s, s, s, sign));
+        add_exchange_steps(p, v, s, s - 1, mode);
+      }
+      for (int a = g; a <= d - 2; ++a) v.push_back(fft_step(p, a, 0, 0, sign));
+      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+    }
+  }
+  // normalisation on the last FFT pass of the scaled direction
+  const bool scale_here = (sign == TFFT_FORWARD) == !(p->flags & TFFT_NORM_BACKWARD);
+  if (scale_here) {
+    for (int k = (int)v.size() - 1; k >= 0; --k)
+      if (v[k].kind != S_BOX) {
+        v[k].scaled = true;
+        v[k].scale_value = 1.0 / (double)p->nelems;
+        break;
+      }
+  }
+  return v;
+}
+
+// Assign buffers: the first step reads the input; in-place passes keep the
+// current buffer (the input itself only when it may be overwritten);
+// layout-changing steps alternate between the work buffers; the last
+// layout-changing step (or the first pass when there is none) writes `out`.
+void assign_buffers(std::vector<Step>& v, bool destroy_input) {
+  int last_move = -1;
+  for (int k = 0; k < (int)v.size(); ++k)
+    if (!v[k].inplace_ok) last_move = k;
+  int cur = BUF_IN;
+  for (int k = 0; k < (int)v.size(); ++k) {
+    Step& s = v[k];
+    s.src = cur;
+    if (s.inplace_ok) {
+      if (cur == BUF_IN) {
+        if (last_move < k) s.dst = BUF_OUT;
+        else s.dst = destroy_input ? BUF_IN : BUF_W0;
+      } else {
+        s.dst = cur;
+      }
+    } else {
+      if (k == last_move) s.dst = BUF_OUT;
+      else s.dst = (cur == BUF_W0) ? BUF_W1 : BUF_W0;
+    }
+    cur = s.dst;
+  }
+}
+
+int check_ptr(const void* ptr, const char* name) {
+  if (!ptr) return fail(TFFT_EINVAL, std::string(name) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(ptr) & 15)
+    return fail(TFFT_EALIGN, std::string(name) + " is not 16-byte aligned");
+  return TFFT_OK;
+}
+
+int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) {
+  const float2* in = static_cast<const float2*>(bufs[s.src]);
+  float2* out = static_cast<float2*>(bufs[s.dst]);
+  cudaError_t e = cudaSuccess;
+  if (s.kind == S_CONTIG) {
+    ContigArgs a;
+    a.in = in;
+    a.out = out;
+    a.nlines = s.nlines;
+    a.ap = p->aplan[s.L];
+    a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
+    a.lines_per_cta = std::max(1, 256 / a.ap.T);
+    a.sign = s.sign;
+    a.scale = s.scaled ? (float)s.scale_value : 1.0f;
+    e = launch_contig(a, st);
+  } else if (s.kind == S_STRIDED) {
+    StridedArgs a;
+    a.in = in;
+    a.out = out;
+    a.lin = dev_layout(p, p->st[s.lin]);
+    a.lout = dev_layout(p, p->st[s.lout]);
+    a.d = p->d;
+    a.axis = s.axis;
+    a.ap = p->aplan_s[s.L];
+    a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
+    a.colblocks = reinterpret_cast<const int2*>(p->d_state + s.cb_off);
+    a.ncolblocks = s.ncb;
+    int oax[2] = {-1, -1}, no = 0;
+    int64_t nouter = 1;
+    for (int m = 0; m < p->d - 1; ++m)
+      if (m != s.axis) {
+        oax[no++] = m;
+        nouter *= p->cshape[m];
+      }
+    a.nouter = nouter;
+    a.oax0 = oax[0];
+    a.oax1 = oax[1];
+    a.on1 = oax[1] >= 0 ? p->cshape[oax[1]] : 1;
+    a.W = s.W;
+    a.sign = s.sign;
+    a.scale = s.scaled ? (float)s.scale_value : 1.0f;
+    e = launch_strided(a, st);
+  } else {
+    BoxArgs a;
+    a.in = in;
+    a.out = out;
+    a.boxes = reinterpret_cast<const BoxDesc*>(p->d_state + s.box_off);
+    a.nboxes = s.nboxes;
+    a.vec2 = s.vec2;
+    e = launch_boxcopy(a, s.max_rows, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return TFFT_OK;
+}
+
+int run_steps(tfft_plan p, const std::vector<Step>& steps, void* const* bufs, cudaStream_t st) {
+  const bool timed = !p->events.empty();
+  for (size_t k = 0; k < steps.size(); ++k) {
+    if (timed) {
+      cudaError_t e = cudaEventRecord(p->events[k], st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    }
+    int rc = launch_step(p, steps[k], bufs, st);
+    if (rc != TFFT_OK) return rc;
+  }
+  if (timed) {
+    cudaError_t e = cudaEventRecord(p->events[steps.size()], st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  }
+  return TFFT_OK;
+}
+
+bool is_smooth_235(int64_t n) {
+  if (n < 1) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+}  // namespace
+
+// ============================================================== ABI
+
+extern "C" {
+
+const char* tfft_status_string(int status) {
+  switch (status) {
+    case TFFT_OK: return "TFFT_OK";
+    case TFFT_EINVAL: return "TFFT_EINVAL";
+    case TFFT_EUNSUPPORTED: return "TFFT_EUNSUPPORTED";
+    case TFFT_EALIGN: return "TFFT_EALIGN";
+    case TFFT_EWORKSPACE: return "TFFT_EWORKSPACE";
+    case TFFT_ECUDA: return "TFFT_ECUDA";
+    case TFFT_ESTATE: return "TFFT_ESTATE";
+    default: return "TFFT_UNKNOWN";
+  }
+}
+
+const char* tfft_last_error(void) { return g_err.c_str(); }
+
+int tfft_version(void) { return 100; }
+
+int tfft_decompose(int64_t N, int64_t M, int64_t p, int64_t* n, int64_t* s) {
+  if (!n || !s) return fail(TFFT_EINVAL, "decompose: NULL output");
+  if (N < 0 || M <= 0 || p < 0 || p >= M) return fail(TFFT_EINVAL, "decompose: need N >= 0, M > 0, 0 <= p < M");
+  decompose(N, M, p, *n, *s);
+  return TFFT_OK;
+}
+
+int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_ndims,
+                     const int* grid, int kind, int precision, int flags) {
+  if (!plan) return fail(TFFT_EINVAL, "plan is NULL");
+  *plan = nullptr;
+  if (ndims < 1 || ndims > MAXD) return fail(TFFT_EINVAL, "ndims must be 1..4");
+  if (!shape) return fail(TFFT_EINVAL, "shape is NULL");
+  if (grid_ndims < 0 || grid_ndims > ndims - 1 || grid_ndims > MAXG)
+    return fail(TFFT_EINVAL, "grid_ndims must be 0..min(3, ndims - 1) (Sec. 3.6)");
+  if (grid_ndims > 0 && !grid) return fail(TFFT_EINVAL, "grid is NULL");
+  if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
+  if (kind == TFFT_R2C) return fail(TFFT_EUNSUPPORTED, "real-to-complex plans are not built yet");
+  if (precision != TFFT_FP32) return fail(TFFT_EUNSUPPORTED, "precision must be TFFT_FP32");
+  if (flags & ~TFFT_NORM_BACKWARD) return fail(TFFT_EINVAL, "unknown flag bits");
+  auto p = new tfft_plan_s();
+  p->d = ndims;
+  p->g = grid_ndims;
+  p->kind = kind;
+  p->precision = precision;
+  p->flags = flags;
+  int64_t n = 1;
+  for (int m = 0; m < ndims; ++m) {
+    if (shape[m] < 1 || shape[m] > (int64_t(1) << 31)) {
+      delete p;
+      return fail(TFFT_EINVAL, "every extent must be in 1 .. 2^31");
+    }
+    p->shape[m] = p->cshape[m] = shape[m];
+    n *= shape[m];
+  }
+  p->nelems = n;
+  int64_t nr = 1;
+  for (int i = 0; i < grid_ndims; ++i) {
+    if (grid[i] < 1 || grid[i] > 65536) {
+      delete p;
+      return fail(TFFT_EINVAL, "grid extents must be in 1 .. 65536");
+    }
+    p->grid[i] = grid[i];
+    nr *= grid[i];
+  }
+  if (nr > (1 << 20)) {
+    delete p;
+    return fail(TFFT_EINVAL, "too many virtual ranks");
+  }
+  p->nranks = (int)nr;
+  for (int i = grid_ndims - 1, s = 1; i >= 0; --i) {
+    p->rstride[i] = s;
+    s *= grid[i];
+  }
+  // stage layouts and their rank offset tables
+  p->st.resize(p->g + 1);
+  for (int s = 0; s <= p->g; ++s) {
+    build_layout(p, p->cshape, s, p->st[s]);
+    p->st[s].state_off = image_add(p, p->st[s].offset.data(), p->st[s].offset.size() * 8);
+  }
+  // per-length FFT plans and twiddle table slots (a plan whose lengths do not
+  // factor into 2, 3, 5 up to 4096 still redistributes, but does not transform)
+  for (int m = 0; m < ndims; ++m) {
+    const int L = (int)p->cshape[m];
+    if (p->aplan.count(L)) continue;
+    AxisPlan ap, aps;
+    if (L > MAXLEN || !is_smooth_235(L) || !make_axis_plan(L, false, ap) ||
+        !make_axis_plan(L, true, aps)) {
+      p->transformable = false;
+      continue;
+    }
+    p->aplan[L] = ap;
+    p->aplan_s[L] = aps;
+    p->tw_off[L] = image_add(p, nullptr, (size_t)L * sizeof(float2));
+  }
+  // exchange boxes between adjacent stages, both directions
+  for (int s = 1; s <= p->g; ++s) {
+    build_exchange(p, s - 1, s);
+    build_exchange(p, s, s - 1);
+  }
+  if (p->transformable) {
+    // pass lists
+    for (int sign : {TFFT_FORWARD, TFFT_BACKWARD})
+      for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED})
+        p->steps[{sign, mode}] = build_steps(p, sign, mode);
+    // column blocks for in-place partial transforms of every stage
+    for (int s = 0; s <= p->g; ++s)
+      for (auto& kv : p->aplan_s) get_colblocks(p, s, s, strided_width(kv.second));
+  }
+  p->state_bytes = align_up(p->image.size(), 256);
+  p->image.resize(p->state_bytes, 0);
+  *plan = p;
+  return TFFT_OK;
+}
+
+int tfft_plan_destroy(tfft_plan plan) {
+  if (!plan) return fail(TFFT_EINVAL, "plan is NULL");
+  delete plan;
+  return TFFT_OK;
+}
+
+int tfft_plan_num_stages(tfft_plan p, int* nstages) {
+  if (!p || !nstages) return fail(TFFT_EINVAL, "NULL argument");
+  *nstages = p->g + 1;
+  return TFFT_OK;
+}
+
+int tfft_plan_num_ranks(tfft_plan p, int* nranks) {
+  if (!p || !nranks) return fail(TFFT_EINVAL, "NULL argument");
+  *nranks = p->nranks;
+  return TFFT_OK;
+}
+
+int tfft_plan_stage_axis(tfft_plan p, int stage, int* axis) {
+  if (!p || !axis) return fail(TFFT_EINVAL, "NULL argument");
+  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+  *axis = p->g - stage;
+  return TFFT_OK;
+}
+
+int tfft_plan_stage_elems(tfft_plan p, int stage, int real, int64_t* elems) {
+  if (!p || !elems) return fail(TFFT_EINVAL, "NULL argument");
+  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+  if (real) return fail(TFFT_EINVAL, "not a real-to-complex plan");
+  *elems = p->st[stage].total;
+  return TFFT_OK;
+}
+
+int tfft_plan_local_box(tfft_plan p, int stage, int real, int rank, int64_t* start,
+                        int64_t* size, int64_t* offset) {
+  if (!p || !start || !size || !offset) return fail(TFFT_EINVAL, "NULL argument");
+  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+  if (rank < 0 || rank >= p->nranks) return fail(TFFT_EINVAL, "rank out of range");
+  if (real) return fail(TFFT_EINVAL, "not a real-to-complex plan");
+  const LayoutH& L = p->st[stage];
+  for (int m = 0; m < p->d; ++m) {
+    start[m] = L.start[(size_t)rank * p->d + m];
+    size[m] = L.size[(size_t)rank * p->d + m];
+  }
+  *offset = L.offset[rank];
+  return TFFT_OK;
+}
+
+int tfft_plan_state_bytes(tfft_plan p, size_t* bytes) {
+  if (!p || !bytes) return fail(TFFT_EINVAL, "NULL argument");
+  *bytes = p->state_bytes;
+  return TFFT_OK;
+}
+
+int tfft_plan_bind(tfft_plan p, void* d_state, size_t bytes, void* stream) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  int rc = check_ptr(d_state, "d_state");
+  if (rc) return rc;
+  if (bytes < p->state_bytes) return fail(TFFT_EINVAL, "state buffer too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(d_state, p->image.data(), p->state_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (plan state)");
+  for (auto& kv : p->tw_off) {
+    e = launch_twiddles(reinterpret_cast<float2*>(static_cast<char*>(d_state) + kv.second), kv.first, st);
+    if (e != cudaSuccess) return cuda_fail(e, "twiddle generation");
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (bind)");
+  p->d_state = static_cast<char*>(d_state);
+  return TFFT_OK;
+}
+
+int tfft_plan_workspace_bytes(tfft_plan p, int mode, int keep_input, size_t* bytes) {
+  if (!p || !bytes) return fail(TFFT_EINVAL, "NULL argument");
+  const size_t stage = (size_t)p->nelems * sizeof(float2);
+  switch (mode) {
+    case TFFT_MODE_FUSED: *bytes = keep_input ? stage : 0; break;
+    case TFFT_MODE_UNFUSED:
+    case TFFT_MODE_PACKED: *bytes = 2 * stage; break;
+    default: return fail(TFFT_EINVAL, "unknown mode");
+  }
+  return TFFT_OK;
+}
+
+int tfft_redistribute(tfft_plan p, int axis_v, int axis_w, const void* in, void* out, void* stream) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  const int sf = p->g - axis_v, stt = p->g - axis_w;
+  if (sf < 0 || sf > p->g || stt < 0 || stt > p->g || std::abs(sf - stt) != 1)
+    return fail(TFFT_EINVAL, "axis_v / axis_w are not the aligned axes of two adjacent stages");
+  int rc = check_ptr(in, "in");
+  if (rc) return rc;
+  rc = check_ptr(out, "out");
+  if (rc) return rc;
+  const size_t bytes = (size_t)p->nelems * sizeof(float2);
+  const char* a = static_cast<const char*>(in);
+  const char* b = static_cast<const char*>(out);
+  if (a < b + bytes && b < a + bytes) return fail(TFFT_EINVAL, "in and out overlap");
+  const ExchangeBoxes& X = p->xboxes[{sf, stt}];
+  Step s = box_step(p, X.direct, p->xbox_off[{sf, stt}][0]);
+  s.src = BUF_IN;
+  s.dst = BUF_OUT;
+  void* bufs[4] = {const_cast<void*>(in), out, nullptr, nullptr};
+  return launch_step(p, s, bufs, static_cast<cudaStream_t>(stream));
+}
+
+int tfft_partial(tfft_plan p, int stage, int axis, int sign, void* inout, void* stream) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+  if (axis < 0 || axis >= p->d) return fail(TFFT_EINVAL, "axis out of range");
+  if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
+  if (p->st[stage].owner[axis] >= 0) return fail(TFFT_EINVAL, "axis is distributed in this stage");
+  if (!p->aplan.count((int)p->cshape[axis]))
+    return fail(TFFT_EUNSUPPORTED, "axis length is not a product of 2, 3, 5 up to 4096");
+  int rc = check_ptr(inout, "inout");
+  if (rc) return rc;
+  Step s = fft_step(p, axis, stage, stage, sign);
+  s.src = BUF_IN;
+  s.dst = BUF_IN;
+  if (sign == TFFT_FORWARD) {
+    s.scaled = true;
+    s.scale_value = 1.0 / (double)p->cshape[axis];
+  }
+  void* bufs[4] = {inout, inout, nullptr, nullptr};
+  return launch_step(p, s, bufs, static_cast<cudaStream_t>(stream));
+}
+
+int tfft_plan_num_launches(tfft_plan p, int sign, int mode, int* n) {
+  if (!p || !n) return fail(TFFT_EINVAL, "NULL argument");
+  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length is not a product of 2, 3, 5 up to 4096");
+  auto it = p->steps.find({sign, mode});
+  if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
+  *n = (int)it->second.size();
+  return TFFT_OK;
+}
+
+int tfft_plan_set_launch_events(tfft_plan p, void* const* events, int count) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  if (count < 0 || (count > 0 && !events)) return fail(TFFT_EINVAL, "bad events");
+  p->events.clear();
+  for (int k = 0; k < count; ++k) {
+    if (!events[k]) return fail(TFFT_EINVAL, "NULL event");
+    p->events.push_back(static_cast<cudaEvent_t>(events[k]));
+  }
+  return TFFT_OK;
+}
+
+int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, void* work,
+                 size_t work_bytes, void* stream) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
+  if (mode < TFFT_MODE_FUSED || mode > TFFT_MODE_PACKED) return fail(TFFT_EINVAL, "unknown mode");
+  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length is not a product of 2, 3, 5 up to 4096");
+  int rc = check_ptr(in, "in");
+  if (rc) return rc;
+  rc = check_ptr(out, "out");
+  if (rc) return rc;
+  const size_t stage = (size_t)p->nelems * sizeof(float2);
+  {
+    const char* a = static_cast<const char*>(in);
+    const char* b = static_cast<const char*>(out);
+    if (a < b + stage && b < a + stage) return fail(TFFT_EINVAL, "in and out overlap");
+  }
+  std::vector<Step> steps = p->steps[{sign, mode}];
+  void* w0 = nullptr;
+  void* w1 = nullptr;
+  bool destroy = false;
+  if (mode == TFFT_MODE_FUSED) {
+    if (work) {
+      rc = check_ptr(work, "work");
+      if (rc) return rc;
+      if (work_bytes < stage) return fail(TFFT_EWORKSPACE, "fused workspace must hold one stage buffer");
+      w0 = work;
+    } else {
+      destroy = true;
+    }
+  } else {
+    if (!work || work_bytes < 2 * stage)
+      return fail(TFFT_EWORKSPACE, "this mode needs a workspace of two stage buffers");
+    rc = check_ptr(work, "work");
+    if (rc) return rc;
+    w0 = work;
+    w1 = static_cast<char*>(work) + stage;
+  }
+  if (work) {
+    const char* a = static_cast<const char*>(work);
+    const size_t wb = (mode == TFFT_MODE_FUSED) ? stage : 2 * stage;
+    for (const void* q : {in, static_cast<const void*>(out)}) {
+      const char* b = static_cast<const char*>(q);
+      if (a < b + stage && b < a + wb) return fail(TFFT_EINVAL, "work overlaps in or out");
+    }
+  }
+  assign_buffers(steps, destroy);
+  if (!p->events.empty() && p->events.size() < steps.size() + 1)
+    return fail(TFFT_EINVAL, "fewer launch events than launches + 1");
+  void* bufs[4] = {const_cast<void*>(in), out, w0, w1};
+  return run_steps(p, steps, bufs, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal interface between the host plan code and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tfft_common.cuh"
+
+namespace tfft {
+
+// Batched 1-D FFT of contiguous lines (the axis held whole and innermost,
+// Eq. pencil0 / slab0): line l of the buffer is elements [l L, (l + 1) L).
+struct ContigArgs {
+  const float2* in;
+  float2* out;
+  int64_t nlines;
+  AxisPlan ap;
+  const float2* tw;  // ap.L roots exp(-2 pi i m / L)
+  int lines_per_cta;
+  int sign;
+  float scale;
+};
+
+// 1-D FFT along axis `axis` < d - 1 with the redistribution fused into the
+// loads (input layout lin) and the stores (output layout lout).  A tile is
+// one value of the remaining axes ("outer" index) times a block of up to W
+// consecutive columns of the innermost axis d - 1 that lies inside one rank
+// of both layouts; the kernel gathers each column's full line from whatever
+// virtual ranks hold it and scatters the result the same way.
+struct StridedArgs {
+  const float2* in;
+  float2* out;
+  DevLayout lin;
+  DevLayout lout;
+  int d;
+  int axis;
+  AxisPlan ap;
+  const float2* tw;
+  const int2* colblocks;  // (first column, width) along axis d - 1
+  int64_t ncolblocks;
+  int64_t nouter;
+  int oax0, oax1;         // the outer axes (or -1), outer index = g[oax0] * on1 + g[oax1]
+  int64_t on1;
+  int W;                  // block width (blockDim.x)
+  int sign;
+  float scale;
+};
+
+// Copy of rectangular boxes: each box has up to MAXD extents, a source and a
+// destination base offset and per-axis strides (the innermost stride is 1 on
+// both sides).  This is the all-to-all of subarray types of Alg. 3 on the
+// virtual grid, and the pack / contiguous exchange / unpack of the
+// traditional method.
+struct BoxDesc {
+  int64_t src;
+  int64_t dst;
+  int64_t ext[MAXD];
+  int64_t ss[MAXD];
+  int64_t ds[MAXD];
+};
+
+struct BoxArgs {
+  const float2* in;
+  float2* out;
+  const BoxDesc* boxes;
+  int nboxes;
+  int vec2;  // every offset, stride and innermost extent is even: copy pairs
+};
+
+cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s);
+cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
+cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s);
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+
+// Limits of the kernels, used by the planner.
+bool kernel_supports_E(int E);
+
+}  // namespace tfft

@@ -1,0 +1,374 @@
+// CUDA kernels of the transpose-algorithm FFT on a virtual process grid
+// (sm_103a).  Every 1-D FFT runs as a self-sorting Stockham schedule (see
+// tfft_common.cuh): each thread keeps E elements of a line in registers, the
+// radix-R butterflies of a stage run on them, and the line is exchanged
+// through shared memory between stages.  Global memory is touched once per
+// element per pass: the first stage loads straight from HBM and the last
+// stage stores straight to HBM.
+#include <type_traits>
+
+#include "tfft_internal.h"
+
+namespace tfft {
+
+namespace {
+
+template <int E, class F>
+__device__ __forceinline__ void with_radix(int R, F&& f) {
+  switch (R) {
+    case 2:
+      if constexpr (E % 2 == 0) f(std::integral_constant<int, 2>{});
+      break;
+    case 3:
+      if constexpr (E % 3 == 0) f(std::integral_constant<int, 3>{});
+      break;
+    case 4:
+      if constexpr (E % 4 == 0) f(std::integral_constant<int, 4>{});
+      break;
+    case 5:
+      if constexpr (E % 5 == 0) f(std::integral_constant<int, 5>{});
+      break;
+    case 8:
+      if constexpr (E % 8 == 0) f(std::integral_constant<int, 8>{});
+      break;
+    case 16:
+      if constexpr (E % 16 == 0) f(std::integral_constant<int, 16>{});
+      break;
+    default:
+      break;
+  }
+}
+
+// Twiddle and butterfly of the E / R work items a thread owns in one stage.
+// Work item q of thread jt is j = jt + q T; its inputs sit in v[q R + r].
+template <int E, int R>
+__device__ __forceinline__ void radix_stage(float2 (&v)[E], int jt, int T, int Ns, int L,
+                                            const float2* __restrict__ tw) {
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    if (Ns > 1) {
+      const int j = jt + q * T;
+      const int step = (j % Ns) * (L / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], __ldg(&tw[r * step]));
+    }
+    Dft<R>::run(&v[q * R]);
+  }
+}
+
+__device__ __forceinline__ int padpos(int pos) { return pos + (pos >> 4); }
+
+// ------------------------------------------------------------ contiguous lines
+
+template <int E>
+__global__ void __launch_bounds__(512, 2) k_fft_contig(const ContigArgs a) {
+  extern __shared__ float2 smem[];
+  const int L = a.ap.L, T = a.ap.T, nst = a.ap.nst;
+  const int jt = threadIdx.x, ly = threadIdx.y, B = blockDim.y;
+  const int Lp = L + (L >> 4);
+  float2* sl = smem + ly * Lp;
+  const bool inv = a.sign > 0;
+  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
+    const int64_t line = base + ly;
+    const bool act = line < a.nlines;
+    const float2* src = a.in + line * L;
+    float2* dst = a.out + line * L;
+    if (nst == 0) {  // length-1 axis: the DFT is the identity
+      if (act && jt == 0) dst[0] = cscale(src[0], a.scale);
+      continue;
+    }
+    float2 v[E];
+    int Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+      const int R = stage_radix(a.ap.code, s);
+      if (s == 0) {
+        with_radix<E>(R, [&](auto rc) {
+          constexpr int RR = decltype(rc)::value;
+#pragma unroll
+          for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+              const int pos = jt + q * T + r * (L / RR);
+              float2 x = act ? src[pos] : make_float2(0.f, 0.f);
+              if (inv) x.y = -x.y;
+              v[q * RR + r] = x;
+            }
+        });
+      } else {
+        const int Rp = stage_radix(a.ap.code, s - 1);
+        const int Nsp = Ns / Rp;
+        __syncthreads();
+        with_radix<E>(Rp, [&](auto rc) {
+          constexpr int RR = decltype(rc)::value;
+#pragma unroll
+          for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+            for (int r = 0; r < RR; ++r)
+              sl[padpos(stockham_out_index(jt + q * T, Nsp, RR, r))] = v[q * RR + r];
+        });
+        __syncthreads();
+        with_radix<E>(R, [&](auto rc) {
+          constexpr int RR = decltype(rc)::value;
+#pragma unroll
+          for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+            for (int r = 0; r < RR; ++r) v[q * RR + r] = sl[padpos(jt + q * T + r * (L / RR))];
+        });
+      }
+      with_radix<E>(R, [&](auto rc) {
+        constexpr int RR = decltype(rc)::value;
+        radix_stage<E, RR>(v, jt, T, Ns, L, a.tw);
+      });
+      Ns *= R;
+    }
+    with_radix<E>(stage_radix(a.ap.code, nst - 1), [&](auto rc) {
+      constexpr int RR = decltype(rc)::value;
+#pragma unroll
+      for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          float2 x = cscale(v[q * RR + r], a.scale);
+          if (inv) x.y = -x.y;
+          if (act) dst[jt + q * T + r * (L / RR)] = x;
+        }
+    });
+  }
+}
+
+// ------------------------------------------------------------ strided lines
+
+template <int E>
+__global__ void __launch_bounds__(512, 1) k_fft_strided(const StridedArgs a) {
+  extern __shared__ float2 smem[];
+  const int L = a.ap.L, T = a.ap.T, nst = a.ap.nst, W = a.W;
+  const int cx = threadIdx.x, jt = threadIdx.y;
+  const int tid = jt * W + cx, nthr = W * T;
+  int64_t* rin = reinterpret_cast<int64_t*>(smem + (size_t)L * W);
+  int64_t* rout = rin + L;
+  const bool inv = a.sign > 0;
+  const int64_t ntiles = a.nouter * a.ncolblocks;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t o = tile / a.ncolblocks;
+    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
+    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    __syncthreads();  // the previous tile is done with the row tables
+    for (int i = tid; i < L; i += nthr) {
+      int64_t g[MAXD];
+#pragma unroll
+      for (int m = 0; m < MAXD; ++m)
+        g[m] = (m == a.axis) ? (int64_t)i
+             : (m == a.d - 1) ? (int64_t)blk.x
+             : (m == a.oax0) ? go0
+             : (m == a.oax1) ? go1
+                             : 0;
+      rin[i] = layout_addr(a.lin, g[0], g[1], g[2], g[3]);
+      rout[i] = layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+    }
+    __syncthreads();
+    const bool act = cx < blk.y;
+    if (nst == 0) {
+      if (act && jt == 0) a.out[rout[0] + cx] = cscale(a.in[rin[0] + cx], a.scale);
+      continue;
+    }
+    float2 v[E];
+    int Ns = 1;
+    for (int s = 0; s < nst; ++s) {
+      const int R = stage_radix(a.ap.code, s);
+      if (s == 0) {
+        with_radix<E>(R, [&](auto rc) {
+          constexpr int RR = decltype(rc)::value;
+#pragma unroll
+          for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+              const int pos = jt + q * T + r * (L / RR);
+              float2 x = act ? a.in[rin[pos] + cx] : make_float2(0.f, 0.f);
+              if (inv) x.y = -x.y;
+              v[q * RR + r] = x;
+            }
+        });
+      } else {
+        const int Rp = stage_radix(a.ap.code, s - 1);
+        const int Nsp = Ns / Rp;
+        __syncthreads();
+        with_radix<E>(Rp, [&](auto rc) {
+          constexpr int RR = decltype(rc)::value;
+#pragma unroll
+          for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+            for (int r = 0; r < RR; ++r)
+              smem[stockham_out_index(jt + q * T, Nsp, RR, r) * W + cx] = v[q * RR + r];
+        });
+        __syncthreads();
+        with_radix<E>(R, [&](auto rc) {
+          constexpr int RR = decltype(rc)::value;
+#pragma unroll
+          for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+            for (int r = 0; r < RR; ++r)
+              v[q * RR + r] = smem[(jt + q * T + r * (L / RR)) * W + cx];
+        });
+      }
+      with_radix<E>(R, [&](auto rc) {
+        constexpr int RR = decltype(rc)::value;
+        radix_stage<E, RR>(v, jt, T, Ns, L, a.tw);
+      });
+      Ns *= R;
+    }
+    with_radix<E>(stage_radix(a.ap.code, nst - 1), [&](auto rc) {
+      constexpr int RR = decltype(rc)::value;
+#pragma unroll
+      for (int q = 0; q < E / RR; ++q)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          const int pos = jt + q * T + r * (L / RR);
+          float2 x = cscale(v[q * RR + r], a.scale);
+          if (inv) x.y = -x.y;
+          if (act) a.out[rout[pos] + cx] = x;
+        }
+    });
+  }
+}
+
+// ------------------------------------------------------------ box copy
+
+__global__ void __launch_bounds__(256) k_boxcopy(const BoxArgs a) {
+  const BoxDesc* bp = a.boxes + blockIdx.y;
+  const int64_t e0 = bp->ext[0], e1 = bp->ext[1], e2 = bp->ext[2];
+  const int64_t rowlen = a.vec2 ? bp->ext[3] / 2 : bp->ext[3];  // in copy units
+  const int64_t nrows = e0 * e1 * e2;
+  if (nrows == 0 || rowlen == 0) return;
+  // lanes per row: the smallest power of two >= rowlen, at most 32
+  int lpr = 1;
+  while (lpr < 32 && lpr < rowlen) lpr <<= 1;
+  const int rpw = 32 / lpr;  // rows per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  const int sub = lane / lpr, l = lane - sub * lpr;
+  const int64_t s0 = bp->ss[0], s1 = bp->ss[1], s2 = bp->ss[2];
+  const int64_t d0 = bp->ds[0], d1 = bp->ds[1], d2 = bp->ds[2];
+  const int64_t sb = bp->src, db = bp->dst;
+  for (int64_t row = ((int64_t)blockIdx.x * wpc + warp) * rpw + sub; row < nrows;
+       row += (int64_t)gridDim.x * wpc * rpw) {
+    const int64_t i2 = row % e2;
+    const int64_t t = row / e2;
+    const int64_t i1 = t % e1;
+    const int64_t i0 = t / e1;
+    const int64_t so = sb + i0 * s0 + i1 * s1 + i2 * s2;
+    const int64_t dof = db + i0 * d0 + i1 * d1 + i2 * d2;
+    if (a.vec2) {
+      const float4* src = reinterpret_cast<const float4*>(a.in + so);
+      float4* dst = reinterpret_cast<float4*>(a.out + dof);
+      for (int64_t c = l; c < rowlen; c += lpr) dst[c] = src[c];
+    } else {
+      const float2* src = a.in + so;
+      float2* dst = a.out + dof;
+      for (int64_t c = l; c < rowlen; c += lpr) dst[c] = src[c];
+    }
+  }
+}
+
+// ------------------------------------------------------------ twiddles
+
+// exp(-2 pi i m / L) for m < L, evaluated in double precision and rounded to
+// float (the only double-precision arithmetic of the path besides the
+// normalisation factor).
+__global__ void k_twiddles(float2* tw, int L) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < L) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)L, &s, &c);
+    tw[m] = make_float2((float)c, (float)(-s));
+  }
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+constexpr int64_t kMaxGrid = 1 << 20;
+
+template <int E>
+cudaError_t launch_contig_E(const ContigArgs& a, cudaStream_t s) {
+  static cudaError_t attr = allow_smem(k_fft_contig<E>);
+  if (attr != cudaSuccess) return attr;
+  const int B = a.lines_per_cta;
+  const int L = a.ap.L;
+  const size_t smem = (size_t)B * (L + (L >> 4)) * sizeof(float2);
+  int64_t grid = (a.nlines + B - 1) / B;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaSuccess;
+  k_fft_contig<E><<<(unsigned)grid, dim3(a.ap.T, B), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int E>
+cudaError_t launch_strided_E(const StridedArgs& a, cudaStream_t s) {
+  static cudaError_t attr = allow_smem(k_fft_strided<E>);
+  if (attr != cudaSuccess) return attr;
+  const int L = a.ap.L;
+  const size_t smem = (size_t)L * a.W * sizeof(float2) + 2 * (size_t)L * sizeof(int64_t);
+  int64_t grid = a.nouter * a.ncolblocks;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaSuccess;
+  k_fft_strided<E><<<(unsigned)grid, dim3(a.W, a.ap.T), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define TFFT_FOR_EACH_E(X) \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(8) X(10) X(12) X(15) X(16) X(20) X(24)
+
+bool kernel_supports_E(int E) {
+  switch (E) {
+#define X(e) case e:
+    TFFT_FOR_EACH_E(X)
+#undef X
+    return true;
+    default:
+      return false;
+  }
+}
+
+cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
+  switch (a.ap.E) {
+#define X(e) \
+  case e:    \
+    return launch_contig_E<e>(a, s);
+    TFFT_FOR_EACH_E(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
+  switch (a.ap.E) {
+#define X(e) \
+  case e:    \
+    return launch_strided_E<e>(a, s);
+    TFFT_FOR_EACH_E(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s) {
+  if (a.nboxes <= 0) return cudaSuccess;
+  if (a.nboxes > 65535) return cudaErrorInvalidConfiguration;
+  int64_t gx = (max_rows + 7) / 8;  // 8 warps, at least one row each
+  if (gx < 1) gx = 1;
+  if (gx > 65535) gx = 65535;
+  k_boxcopy<<<dim3((unsigned)gx, (unsigned)a.nboxes), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s) {
+  k_twiddles<<<(L + 255) / 256, 256, 0, s>>>(tw, L);
+  return cudaGetLastError();
+}
+
+}  // namespace tfft

@@ -1,0 +1,206 @@
+"""Python front end of the C ABI: a plan over a global shape and a virtual grid.
+
+PyTorch supplies device memory and streams only; every step of the transform
+runs in the library's CUDA kernels.  All buffers are caller-owned torch
+tensors passed as raw pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _lib
+from ._lib import call
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_MODES = {"fused": _lib.TFFT_MODE_FUSED, "unfused": _lib.TFFT_MODE_UNFUSED,
+          "packed": _lib.TFFT_MODE_PACKED}
+
+
+class Plan:
+    """Transpose-algorithm FFT plan (slab: len(grid) == 1, pencil: 2, ...).
+
+    Stage buffers are 1-D complex64 tensors holding every virtual rank's local
+    array, concatenated in rank order.  ``forward`` maps stage 0 to stage g,
+    ``inverse`` stage g to stage 0; ``redistribute(v, w)`` is the exchange of
+    Alg. 3 between the stages aligned in v and in w.
+    """
+
+    def __init__(self, shape, grid, kind: str = "c2c", norm: str = "forward", device=None,
+                 bind: bool = True):
+        self.shape = tuple(int(n) for n in shape)
+        self.grid = tuple(int(m) for m in grid)
+        self.kind = kind
+        kind_id = {"c2c": _lib.TFFT_C2C, "r2c": _lib.TFFT_R2C}[kind]
+        flags = {"forward": _lib.TFFT_NORM_FORWARD, "backward": _lib.TFFT_NORM_BACKWARD}[norm]
+        h = ctypes.c_void_p()
+        shp = (ctypes.c_int64 * len(self.shape))(*self.shape)
+        grd = (ctypes.c_int * max(1, len(self.grid)))(*(self.grid or (1,)))
+        call("tfft_plan_create", ctypes.byref(h), len(self.shape), shp, len(self.grid), grd,
+             kind_id, _lib.TFFT_FP32, flags)
+        self._h = h
+        self.d = len(self.shape)
+        self.g = len(self.grid)
+        self.device = torch.device(device) if device is not None else None
+        self.state = None
+        self._work = {}
+        if bind:
+            self.bind(device)
+
+    # ------------------------------------------------------------ lifetime
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.load().tfft_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def bind(self, device=None):
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        nbytes = ctypes.c_size_t()
+        call("tfft_plan_state_bytes", self._h, ctypes.byref(nbytes))
+        self.state = torch.empty(max(256, nbytes.value), dtype=torch.uint8, device=dev)
+        with torch.cuda.device(dev):
+            call("tfft_plan_bind", self._h, _ptr(self.state), self.state.numel(), _stream_ptr())
+        return self
+
+    # ------------------------------------------------------------ queries
+    @property
+    def num_stages(self) -> int:
+        n = ctypes.c_int()
+        call("tfft_plan_num_stages", self._h, ctypes.byref(n))
+        return n.value
+
+    @property
+    def num_ranks(self) -> int:
+        n = ctypes.c_int()
+        call("tfft_plan_num_ranks", self._h, ctypes.byref(n))
+        return n.value
+
+    def stage_axis(self, stage: int) -> int:
+        n = ctypes.c_int()
+        call("tfft_plan_stage_axis", self._h, stage, ctypes.byref(n))
+        return n.value
+
+    def stage_elems(self, stage: int, real: bool = False) -> int:
+        n = ctypes.c_int64()
+        call("tfft_plan_stage_elems", self._h, stage, int(real), ctypes.byref(n))
+        return n.value
+
+    def local_box(self, stage: int, rank: int, real: bool = False):
+        st = (ctypes.c_int64 * self.d)()
+        sz = (ctypes.c_int64 * self.d)()
+        off = ctypes.c_int64()
+        call("tfft_plan_local_box", self._h, stage, int(real), rank, st, sz, ctypes.byref(off))
+        return tuple(st), tuple(sz), off.value
+
+    def workspace_bytes(self, mode: str = "fused", keep_input: bool = True) -> int:
+        n = ctypes.c_size_t()
+        call("tfft_plan_workspace_bytes", self._h, _MODES[mode], int(keep_input), ctypes.byref(n))
+        return n.value
+
+    def num_launches(self, sign: int, mode: str = "fused") -> int:
+        n = ctypes.c_int()
+        call("tfft_plan_num_launches", self._h, sign, _MODES[mode], ctypes.byref(n))
+        return n.value
+
+    # ------------------------------------------------------------ buffers
+    def empty_stage(self, stage: int, real: bool = False) -> torch.Tensor:
+        dt = torch.float32 if real else torch.complex64
+        return torch.empty(self.stage_elems(stage, real), dtype=dt, device=self.device)
+
+    def workspace(self, mode: str = "fused", keep_input: bool = True) -> torch.Tensor | None:
+        nb = self.workspace_bytes(mode, keep_input)
+        if nb == 0:
+            return None
+        key = (mode, keep_input)
+        w = self._work.get(key)
+        if w is None or w.numel() < nb:
+            w = torch.empty(nb, dtype=torch.uint8, device=self.device)
+            self._work[key] = w
+        return w
+
+    # ------------------------------------------------------------ transforms
+    def execute(self, sign: int, x: torch.Tensor, out: torch.Tensor, mode: str = "fused",
+                work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        wp = _ptr(work) if work is not None else ctypes.c_void_p(0)
+        wb = work.numel() * work.element_size() if work is not None else 0
+        call("tfft_execute", self._h, sign, _MODES[mode], _ptr(x), _ptr(out), wp, wb, _stream_ptr(stream))
+        return out
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, mode: str = "fused",
+                keep_input: bool = True, stream=None) -> torch.Tensor:
+        if out is None:
+            out = self.empty_stage(self.g)
+        work = self.workspace(mode, keep_input)
+        return self.execute(_lib.TFFT_FORWARD, x, out, mode, work, stream)
+
+    def inverse(self, y: torch.Tensor, out: torch.Tensor | None = None, mode: str = "fused",
+                keep_input: bool = True, stream=None) -> torch.Tensor:
+        if out is None:
+            out = self.empty_stage(0, real=(self.kind == "r2c"))
+        work = self.workspace(mode, keep_input)
+        return self.execute(_lib.TFFT_BACKWARD, y, out, mode, work, stream)
+
+    def redistribute(self, axis_v: int, axis_w: int, x: torch.Tensor, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+        if out is None:
+            out = self.empty_stage(self.g - axis_w)
+        call("tfft_redistribute", self._h, axis_v, axis_w, _ptr(x), _ptr(out), _stream_ptr(stream))
+        return out
+
+    def partial(self, stage: int, axis: int, sign: int, x: torch.Tensor, stream=None) -> torch.Tensor:
+        call("tfft_partial", self._h, stage, axis, sign, _ptr(x), _stream_ptr(stream))
+        return x
+
+    def set_launch_events(self, events):
+        """Record torch.cuda.Event objects around every launch of later executes."""
+        if not events:
+            call("tfft_plan_set_launch_events", self._h, None, 0)
+            return
+        handles = []
+        for ev in events:
+            if not ev.cuda_event:
+                ev.record()  # creates the underlying cudaEvent_t
+            handles.append(ev.cuda_event)
+        arr = (ctypes.c_void_p * len(handles))(*handles)
+        call("tfft_plan_set_launch_events", self._h, arr, len(handles))
+
+    # ------------------------------------------------------------ host helpers (tests / IO)
+    def scatter(self, x: torch.Tensor, stage: int = 0, real: bool = False) -> torch.Tensor:
+        """Global array -> stage buffer (each rank's block in rank order).  Not the hot path."""
+        parts = []
+        for r in range(self.num_ranks):
+            st, sz, _ = self.local_box(stage, r, real)
+            sl = tuple(slice(a, a + n) for a, n in zip(st, sz))
+            parts.append(x[sl].reshape(-1))
+        return torch.cat(parts)
+
+    def gather(self, buf: torch.Tensor, stage: int, real: bool = False) -> torch.Tensor:
+        """Stage buffer -> global array.  Not the hot path."""
+        shape = self.shape if (real or self.kind == "c2c") else self.shape[:-1] + (self.shape[-1] // 2 + 1,)
+        out = torch.empty(shape, dtype=buf.dtype, device=buf.device)
+        for r in range(self.num_ranks):
+            st, sz, off = self.local_box(stage, r, real)
+            n = math.prod(sz)
+            sl = tuple(slice(a, a + k) for a, k in zip(st, sz))
+            out[sl] = buf[off:off + n].reshape(sz)
+        return out

@@ -1,0 +1,110 @@
+"""C-ABI library: loads, exports every declared symbol, host-side plan queries (CPU only).
+
+No compute call is made here: plan creation and layout queries are host code.
+"""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+from oracle import decomp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tfft.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_09536_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tfft_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_functions():
+    names = declared_functions()
+    assert "tfft_execute" in names and "tfft_redistribute" in names and len(names) >= 15
+
+
+def test_every_declared_symbol_exported(lib):
+    from paper_1804_09536_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"{name} has no binding"
+
+
+def test_decompose_abi_matches_oracle(lib):
+    n = ctypes.c_int64()
+    s = ctypes.c_int64()
+    for N in range(0, 40):
+        for M in range(1, 9):
+            for p in range(M):
+                assert lib.tfft_decompose(N, M, p, ctypes.byref(n), ctypes.byref(s)) == 0
+                assert (n.value, s.value) == decomp.decompose(N, M, p)
+    assert lib.tfft_decompose(4, 0, 0, ctypes.byref(n), ctypes.byref(s)) == 1
+    assert lib.tfft_decompose(4, 2, 2, ctypes.byref(n), ctypes.byref(s)) == 1
+
+
+@pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((512, 512, 512), (4, 8)),
+                                        ((42, 127, 256), (3, 4)), ((256, 256, 256), (8,)),
+                                        ((3, 2, 5), (4, 3)), ((16, 17, 18, 20), (2, 3, 2)),
+                                        ((64, 128, 256), (2, 4)), ((8,), ())])
+def test_plan_layouts_match_oracle(lib, shape, grid):
+    from paper_1804_09536_gb300.plan import Plan
+    p = Plan(shape, grid, bind=False)
+    assert p.num_stages == len(grid) + 1
+    assert p.num_ranks == math.prod(grid)
+    for s in range(len(grid) + 1):
+        layout, total = decomp.stage_layout(shape, grid, s)
+        assert p.stage_elems(s) == total
+        assert p.stage_axis(s) == decomp.aligned_axis(len(shape), grid, s)
+        for r, (st, sz, off) in enumerate(layout):
+            assert p.local_box(s, r) == (st, sz, off)
+
+
+def test_unsupported_and_invalid(lib):
+    from paper_1804_09536_gb300.plan import Plan
+    from paper_1804_09536_gb300._lib import TfftError
+    p = Plan((7, 8, 8), (2, 2), bind=False)  # prime length: plans and redistributes ...
+    with pytest.raises(TfftError) as e:
+        p.num_launches(-1)                     # ... but does not transform
+    assert e.value.status == 2
+    with pytest.raises(TfftError) as e:
+        Plan((8, 8, 8), (2, 2, 2), bind=False)
+    assert e.value.status == 1  # grid_ndims > ndims - 1 (Sec. 3.6)
+    with pytest.raises(TfftError):
+        Plan((8, 8, 8), (0, 2), bind=False)
+    with pytest.raises(TfftError):
+        Plan((0, 8, 8), (2, 2), bind=False)
+
+
+def test_calls_validate_before_launch(lib):
+    """Unbound plan and bad pointers are rejected without touching a GPU."""
+    from paper_1804_09536_gb300.plan import Plan
+    p = Plan((8, 8, 8), (2, 2), bind=False)
+    rc = lib.tfft_execute(p.handle, -1, 0, ctypes.c_void_p(16), ctypes.c_void_p(4096),
+                          None, 0, None)
+    assert rc == 6  # TFFT_ESTATE: not bound
+    rc = lib.tfft_redistribute(p.handle, 2, 1, ctypes.c_void_p(16), ctypes.c_void_p(4096), None)
+    assert rc == 6
+    rc = lib.tfft_plan_bind(p.handle, ctypes.c_void_p(8), 1 << 20, None)
+    assert rc == 3  # TFFT_EALIGN
+    rc = lib.tfft_plan_bind(p.handle, None, 1 << 20, None)
+    assert rc == 1
+
+
+def test_launch_counts(lib):
+    from paper_1804_09536_gb300.plan import Plan
+    p = Plan((32, 32, 32), (2, 2), bind=False)
+    assert p.num_launches(-1, "fused") == 3
+    assert p.num_launches(1, "fused") == 3
+    assert p.num_launches(-1, "unfused") == 5
+    # packed: the 2 -> 1 exchange needs pack + all-to-all + unpack, 1 -> 0 needs pack + all-to-all
+    assert p.num_launches(-1, "packed") >= 7

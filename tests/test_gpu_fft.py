@@ -1,0 +1,156 @@
+"""GPU parity: whole transforms vs the FP64 oracle (needs a GPU).
+
+rel-L2 <= 1e-5 against the oracle for the fused path and both comparison
+paths; the three paths run the same butterflies on every line, so their
+outputs must also agree bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import dft, redistribute as R
+from paper_1804_09536_gb300 import inputs
+from gpu_util import RTOL_FP32, bits, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ((32, 32, 32), (2, 2)),          # the 32^3 pencil 2 x 2 parity workload
+    ((8, 8, 8), (2, 2)),
+    ((6, 10, 12), (3, 2)),           # mixed radix 2/3/5, uneven decomposition
+    ((12, 12, 12), (3, 4)),
+    ((64, 128, 256), (2, 4)),        # batch shape, several tiles per pass
+    ((96, 40, 160), (2, 2)),         # radix 3 and 5 lengths
+    ((16, 32, 64), (4,)),            # slab
+    ((5, 6, 8), (4, 3)),             # zero-size ranks on axis 0
+    ((12, 10, 8, 6), (2, 3, 2)),     # 4-D on a 3-D grid
+    ((64, 96), (4,)),                # 2-D slab
+    ((128,), ()),                    # 1-D, no grid
+    ((1, 16, 8), (1, 2)),            # length-1 axis
+]
+
+
+def _run(p, x_dev, mode, sign, keep=True):
+    if sign < 0:
+        return p.forward(x_dev, mode=mode, keep_input=keep)
+    return p.inverse(x_dev, mode=mode, keep_input=keep)
+
+
+@pytest.mark.parametrize("shape,grid", CASES)
+def test_forward_inverse_vs_oracle(cuda_device, shape, grid):
+    from paper_1804_09536_gb300.plan import Plan
+    g = len(grid)
+    x = inputs.uniform_complex(shape, seed=0).numpy()
+    b0 = R.scatter(x, grid, 0)
+    want_f = dft.distributed_forward(b0.astype(np.complex128), shape, grid)
+    want_b = dft.distributed_backward(R.scatter(x, grid, g).astype(np.complex128), shape, grid)
+    p = Plan(shape, grid, device=cuda_device)
+    outs_f, outs_b = {}, {}
+    for mode in ("fused", "unfused", "packed"):
+        xin = to_dev(b0, cuda_device)
+        y = _run(p, xin, mode, -1)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(xin), b0.view(np.uint8)), "input must be kept"
+        err = rel_l2(y.cpu().numpy(), want_f)
+        assert err <= RTOL_FP32, (mode, err)
+        outs_f[mode] = bits(y)
+        yin = to_dev(R.scatter(x, grid, g), cuda_device)
+        z = _run(p, yin, mode, +1)
+        torch.cuda.synchronize()
+        err = rel_l2(z.cpu().numpy(), want_b)
+        assert err <= RTOL_FP32, (mode, err)
+        outs_b[mode] = bits(z)
+    assert np.array_equal(outs_f["fused"], outs_f["unfused"])
+    assert np.array_equal(outs_f["fused"], outs_f["packed"])
+    assert np.array_equal(outs_b["fused"], outs_b["unfused"])
+    assert np.array_equal(outs_b["fused"], outs_b["packed"])
+
+
+@pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((42, 40, 48), (3, 4))])
+def test_round_trip_and_destroyed_input(cuda_device, shape, grid):
+    """App. A: backward(forward(x)) = x; without a workspace the input is scratch."""
+    from paper_1804_09536_gb300.plan import Plan
+    x = inputs.uniform_complex(shape, seed=3).numpy()
+    p = Plan(shape, grid, device=cuda_device)
+    b0 = R.scatter(x, grid, 0)
+    xin = to_dev(b0, cuda_device)
+    y = p.forward(xin, keep_input=False)
+    back = p.inverse(y.clone(), keep_input=False)
+    torch.cuda.synchronize()
+    assert rel_l2(back.cpu().numpy(), b0) <= RTOL_FP32
+
+
+def test_appendix_a_fill_round_trip(cuda_device):
+    """App. A's fill arrayA[j] = j + j i on every local array (scaled to O(1) for FP32),
+    forward then backward on a 2-D grid; FP32 tolerance instead of the paper's FP64 1e-8."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (40, 120, 256), (2, 3)
+    p = Plan(shape, grid, device=cuda_device)
+    buf = np.empty(p.stage_elems(0), np.complex64)
+    for r in range(p.num_ranks):
+        st, sz, off = p.local_box(0, r)
+        n = math.prod(sz)
+        j = np.arange(n, dtype=np.float64) / n
+        buf[off:off + n] = (j + 1j * j).astype(np.complex64)
+    y = p.forward(to_dev(buf, cuda_device))
+    back = p.inverse(y).cpu().numpy()
+    assert np.max(np.abs(back - buf)) < 1e-6
+
+
+@pytest.mark.parametrize("shape,grid", [((16, 24, 32), (2, 2)), ((16, 32, 20), (4,))])
+def test_partial_transforms(cuda_device, shape, grid):
+    """F_axis on every rank's local array (the appendix's sequential routine)."""
+    from paper_1804_09536_gb300.plan import Plan
+    p = Plan(shape, grid, device=cuda_device)
+    x = inputs.normal_complex(shape, seed=5).numpy()
+    g = len(grid)
+    for s in range(g + 1):
+        b = R.scatter(x, grid, s)
+        layout_axes = [a for a in range(len(shape)) if all(
+            p.local_box(s, r)[1][a] == shape[a] for r in range(p.num_ranks))]
+        for axis in layout_axes:
+            for sign in (-1, 1):
+                t = to_dev(b, cuda_device)
+                p.partial(s, axis, sign, t)
+                want = dft._transform_ranks(b.astype(np.complex128), shape, grid, s, axis, sign)
+                assert rel_l2(t.cpu().numpy(), want) <= RTOL_FP32, (s, axis, sign)
+
+
+def test_norm_backward_flag(cuda_device):
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (16, 16, 16), (2, 2)
+    x = inputs.uniform_complex(shape, seed=4).numpy()
+    p = Plan(shape, grid, norm="backward", device=cuda_device)
+    y = p.forward(to_dev(R.scatter(x, grid, 0), cuda_device)).cpu().numpy()
+    want = dft.distributed_forward(R.scatter(x, grid, 0).astype(np.complex128), shape, grid) * 4096
+    assert rel_l2(y, want) <= RTOL_FP32
+
+
+@pytest.mark.slow
+def test_full_size_512_pencil_sampled(cuda_device):
+    """The bench workload (512^3, 4 x 8, launch configuration of bench.py): sampled
+    outputs against the oracle's definition, plus round trip and Parseval."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (512, 512, 512), (4, 8)
+    x = inputs.normal_complex(shape, seed=0)
+    p = Plan(shape, grid, device=cuda_device)
+    b0 = p.scatter(x.to(cuda_device), 0)
+    y = p.forward(b0)
+    yg = p.gather(y, 2).cpu().numpy()
+    rng = np.random.default_rng(0)
+    ks = [(0, 0, 0), (511, 511, 511), (1, 2, 3)] + [tuple(int(v) for v in rng.integers(0, 512, 3))
+                                                   for _ in range(5)]
+    want = dft.forward_at(x.numpy(), ks)
+    got = np.array([yg[k] for k in ks])
+    rms = float(np.sqrt(np.mean(np.abs(yg.astype(np.complex128)) ** 2)))
+    assert np.max(np.abs(got - want)) <= 1e-4 * rms
+    # Parseval (paper normalisation) and round trip hold at any size
+    n = x.numel()
+    e_in = float(torch.sum(torch.abs(x.to(torch.complex128)) ** 2)) / n
+    e_out = float(np.sum(np.abs(yg.astype(np.complex128)) ** 2))
+    assert abs(e_out - e_in) <= 1e-5 * e_in
+    back = p.inverse(y)
+    diff = torch.linalg.vector_norm((back - b0).to(torch.complex128)) / torch.linalg.vector_norm(b0.to(torch.complex128))
+    assert float(diff) <= RTOL_FP32

@@ -186,3 +186,11 @@ def test_distributed_real(shape, grid):
     assert np.allclose(R.gather(y, cshape, grid, len(grid)), dft.rfftn_forward(x), rtol=0, atol=1e-14)
     xb = dft.distributed_irfft_backward(y, shape, grid)
     assert np.allclose(R.gather(xb, shape, grid, 0), x, rtol=0, atol=1e-12)
+
+
+def test_forward_at_matches_full_transform():
+    x = _crand((6, 10, 8), 21)
+    full = dft.fftn_forward(x)
+    ks = [(0, 0, 0), (5, 9, 7), (3, 2, 1), (1, 0, 6)]
+    got = dft.forward_at(x, ks, chunk=4)
+    assert np.allclose(got, [full[k] for k in ks], rtol=0, atol=1e-14)
