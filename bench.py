@@ -1,0 +1,409 @@
+"""Benchmark: 512^3 complex-to-complex FFT, forward + inverse, on a virtual 4 x 8 pencil grid.
+
+One step = one forward and one inverse transform of a seeded 512^3 complex64
+array (Eqs. pencil0-pencil2 and their reverse), redistributions fused into
+the FFT passes.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64 DFT matrices) on a bounded
+sample of the same workload instead.  With N > 1 (torchrun) every rank runs
+its own replica on its own GPU (the path has no cross-GPU exchange); the
+timed region is bracketed by barriers and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (512, 512, 512)
+GRID = (4, 8)
+METRIC = "512^3 c2c fwd+inv ms, 5NlogN GFLOP/s, % HBM roofline; fused vs pack/unpack"
+UNIT = "GFLOP/s"
+
+
+def _set_workload(shape, grid):
+    """Workload constants (the default is the 512^3 4 x 8 headline case; other
+    shapes serve profiling of small cases)."""
+    global SHAPE, GRID, WORKLOAD, N_ELEMS, FLOP_PER_TRANSFORM, FLOP_PER_STEP
+    SHAPE, GRID = tuple(shape), tuple(grid)
+    WORKLOAD = (f"{'x'.join(map(str, SHAPE))} c2c complex64, virtual "
+                f"{'pencil' if len(GRID) == 2 else 'slab' if len(GRID) == 1 else 'grid'} grid "
+                f"{'x'.join(map(str, GRID))}, forward+inverse, fused redistribution")
+    N_ELEMS = math.prod(SHAPE)
+    FLOP_PER_TRANSFORM = 5.0 * N_ELEMS * math.log2(N_ELEMS)   # 5 N log2 N
+    FLOP_PER_STEP = 2.0 * FLOP_PER_TRANSFORM                    # forward + inverse
+
+
+_set_workload(SHAPE, GRID)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tfft_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _traffic_per_launch(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_1804_09536_gb300", "csrc", "tfft_kernels.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        if rec.get("kernels_sha256_16") != h:
+            return None
+        return rec["per_launch_bytes"].get(kernel)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    from paper_1804_09536_gb300.plan import Plan
+    from paper_1804_09536_gb300 import build as _build, inputs
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world > 1:
+        _build.build()
+    plan = Plan(SHAPE, GRID, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # seeded input: complex N(0, 1), the same array on every replica
+    x_host = inputs.normal_complex(SHAPE, seed=0)
+    x = plan.scatter(x_host.to(dev), 0)
+    y = plan.empty_stage(2)
+    z = plan.empty_stage(0)
+    work = plan.workspace("fused", keep_input=True)
+
+    def step(mode="fused", w=work, events=None):
+        if events is not None:
+            plan.set_launch_events(events[0])
+        plan.execute(-1, x, y, mode, w)
+        if events is not None:
+            plan.set_launch_events(events[1])
+        plan.execute(+1, y, z, mode, w)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    nf, nb = plan.num_launches(-1), plan.num_launches(+1)
+    info_f, info_b = plan.launch_info(-1), plan.launch_info(+1)
+    for _ in range(args.warmup):
+        step()
+    # per-launch events for every timed step (recorded on the launching stream)
+    ev = [([torch.cuda.Event(enable_timing=True) for _ in range(nf + 1)],
+           [torch.cuda.Event(enable_timing=True) for _ in range(nb + 1)]) for _ in range(args.steps)]
+    for pair in ev:
+        for e in pair[0] + pair[1]:
+            e.record(stream)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(events=ev[k])
+    t1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    plan.set_launch_events([])
+    total_ms = t0.elapsed_time(t1)
+    per_step = [ev[k][0][0].elapsed_time(ev[k][1][-1]) for k in range(args.steps)]
+    # per-kernel durations over the timed region
+    kern = {}
+    for k in range(args.steps):
+        for evs, info in ((ev[k][0], info_f), (ev[k][1], info_b)):
+            for i, (name, nbytes) in enumerate(info):
+                kern.setdefault(name, {"ms": [], "bytes": nbytes})["ms"].append(evs[i].elapsed_time(evs[i + 1]))
+    gpu_launches = args.steps * (nf + nb)
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * FLOP_PER_STEP / (ms_step * 1e-3) / 1e9
+
+    if args.profile_only:
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "workload": WORKLOAD, "ms_per_step": ms_step,
+                              "kernels": {n: statistics.fmean(r["ms"]) for n, r in kern.items()}}))
+        return
+    # comparison paths, same protocol, fewer steps (outside the headline timing)
+    extra = {}
+    ksteps = max(3, min(args.steps, 20))
+    for mode in ("unfused", "packed"):
+        w2 = plan.workspace(mode)
+        for _ in range(2):
+            step(mode, w2)
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(ksteps):
+            step(mode, w2)
+        b.record(stream)
+        barrier()
+        extra[mode] = a.elapsed_time(b) / ksteps
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # input, forward + inverse, D2H of the result, every step
+    h_in = x.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    esteps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        x.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(z, non_blocking=True)
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(esteps):
+        x.copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(z, non_blocking=True)
+    b.record(stream)
+    barrier()
+    e2e_ms = a.elapsed_time(b) / esteps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    # round-trip check of the last step (the timed work really happened)
+    err = float(torch.linalg.vector_norm(h_out - h_in) / torch.linalg.vector_norm(h_in))
+
+    peak, peak_kind = _peaks()
+    dom = max(kern.items(), key=lambda kv: sum(kv[1]["ms"]))
+    dom_name, dom_rec = dom
+    avg_ms = statistics.fmean(dom_rec["ms"])
+    achieved = dom_rec["bytes"] / (avg_ms * 1e-3) / 1e9
+    step_bytes = sum(nb_ for _, nb_ in info_f + info_b)
+    kernels = {n: {"launches": len(r["ms"]), "avg_ms": round(statistics.fmean(r["ms"]), 4),
+                   "share": round(sum(r["ms"]) / sum(sum(q["ms"]) for q in kern.values()), 4),
+                   "GBps": round(r["bytes"] / (statistics.fmean(r["ms"]) * 1e-3) / 1e9, 1)}
+               for n, r in kern.items()}
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "ms_step_min": round(min(per_step), 4),
+        "ms_step_median": round(statistics.median(per_step), 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: complex N(0,1) per component, torch CPU generator seed 0",
+        "config": {"workload": WORKLOAD, "shape": list(SHAPE), "grid": list(GRID),
+                   "l2": "inputs larger than L2 (1 GiB per stage buffer vs 129 MB L2), no flush",
+                   "replicas": world},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_kind": peak_kind,
+                     "traffic": _traffic_per_launch(dom_name),
+                     "algorithmic_bytes_per_launch": dom_rec["bytes"]},
+        "step_hbm_frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peak, 4),
+        "kernels": kernels,
+        "comparison_ms_per_step": {"fused": round(ms_step, 4),
+                                   "unfused": round(extra["unfused"], 4),
+                                   "packed": round(extra["packed"], 4)},
+        "fused_vs_packed_speedup": round(extra["packed"] / ms_step, 3),
+        "e2e": {"value": round(world * FLOP_PER_STEP / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
+                "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
+                "d2h_bytes_per_step": h_out.numel() * h_out.element_size()},
+        "round_trip_rel_l2": err,
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(target_s=args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- oracle arm
+
+def _oracle_sample(x, k):
+    """The oracle's per-axis DFTs (forward then inverse, axes in the paper's order)
+    over k slices of each axis' lines: fraction k / 512 of one step's arithmetic."""
+    from oracle import dft
+    import numpy as np
+    t = time.perf_counter()
+    blk = x[:k]                                   # lines along axes 2 and 1
+    y = dft.partial_dft(blk, 2, -1)
+    y = dft.partial_dft(y, 1, -1)
+    col = x[:, :k]                                # lines along axis 0
+    c = dft.partial_dft(col, 0, -1)
+    c = dft.partial_dft(c, 0, +1)
+    y = dft.partial_dft(y, 1, +1)
+    y = dft.partial_dft(y, 2, +1)
+    _ = float(np.abs(y[0, 0, 0])) + float(np.abs(c[0, 0, 0]))
+    return time.perf_counter() - t
+
+
+def cpu_baseline(target_s: float = 15.0):
+    from paper_1804_09536_gb300 import inputs
+    x = inputs.normal_complex(SHAPE, seed=0).numpy()
+    t1 = _oracle_sample(x, 4)
+    k = int(max(4, min(SHAPE[0], round(4 * target_s / max(t1, 1e-3)))))
+    secs = _oracle_sample(x, k)
+    frac = k / SHAPE[0]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(frac * FLOP_PER_STEP / secs / 1e9, 4), "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"oracle FP64 exact-angle DFT matrices, forward+inverse along all 3 axes over "
+                      f"{k} of 512 slices ({frac:.4f} of one 512^3 step's lines, {secs:.1f} s), "
+                      f"5NlogN-equivalent flops; redistribution copies not included"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_1804_09536_gb300 import inputs
+    x = inputs.normal_complex(SHAPE, seed=0).numpy()
+    k = 2
+    for _ in range(args.warmup):
+        _oracle_sample(x, k)
+    ts = [_oracle_sample(x, k) for _ in range(args.steps)]
+    frac = k / SHAPE[0]
+    secs = sum(ts) / len(ts)
+    value = frac * FLOP_PER_STEP / secs / 1e9
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = (f"oracle FP64 exact-angle DFT matrices, forward+inverse along all 3 axes over {k} of "
+              f"512 slices per step ({frac:.4f} of the step's lines)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(secs * 1e3 / frac, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic: complex N(0,1), seed 0",
+            "config": {"workload": WORKLOAD, "shape": list(SHAPE), "grid": list(GRID)},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", type=int, nargs="+", default=list(SHAPE))
+    ap.add_argument("--grid", type=int, nargs="*", default=list(GRID))
+    ap.add_argument("--profile-only", action="store_true",
+                    help="headline loop only (no comparison paths, e2e or CPU baseline)")
+    args = ap.parse_args()
+    _set_workload(args.shape, args.grid)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

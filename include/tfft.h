@@ -184,6 +184,15 @@ int tfft_execute(tfft_plan plan, int sign, int mode, const void *in, void *out, 
 int tfft_plan_num_launches(tfft_plan plan, int sign, int mode, int *nlaunches);
 
 /*
+ * Launch `index` of tfft_execute() in a direction and mode: the kernel's
+ * name (NUL-terminated, truncated to name_len) and its algorithmic bytes --
+ * one read and one write of every element it moves (complex64), the figure
+ * a roofline divides by the launch's duration.
+ */
+int tfft_plan_launch_info(tfft_plan plan, int sign, int mode, int index, char *name,
+                          int name_len, int64_t *bytes);
+
+/*
  * Timing hook: record caller-created CUDA events (cudaEvent_t as void*) on
  * the execution stream around every launch of the following tfft_execute()
  * calls: events[k] before launch k and events[n] after the last, n =

@@ -216,10 +216,41 @@ bool make_axis_plan(int L, bool strided, AxisPlan& best) {
       found = true;
     }
   }
+  if (!found) {
+    // no register budget fits every radix: the shared-memory-resident kernel
+    // (E = 0) with a greedy factorisation, largest radices first
+    std::vector<int> f;
+    int rem = L;
+    for (int R : Rs)
+      while (rem % R == 0 && (int)f.size() < MAXSTAGES) {
+        f.push_back(R);
+        rem /= R;
+      }
+    if (rem != 1) return false;
+    int items = 1;
+    for (int R : f) items = std::max(items, L / R);
+    best.L = L;
+    best.E = 0;
+    best.T = std::min(items, strided ? 32 : 128);
+    best.nst = (int)f.size();
+    best.code = 0;
+    for (int s = 0; s < best.nst; ++s) {
+      best.radix[s] = f[s];
+      best.code |= (uint64_t)f[s] << (5 * s);
+    }
+    found = true;
+  }
   return found;
 }
 
-int strided_width(const AxisPlan& ap) { return std::max(1, std::min(32, 512 / ap.T)); }
+int strided_width(const AxisPlan& ap) {
+  int W = std::max(1, std::min(32, 512 / ap.T));
+  // shared memory: L x W elements (two buffers for the generic kernel) + row tables
+  const size_t budget = 200 * 1024 - 16 * (size_t)ap.L;
+  const size_t per_col = (ap.E == 0 ? 2 : 1) * 8 * (size_t)ap.L;
+  while (W > 1 && (size_t)W * per_col > budget) --W;
+  return W;
+}
 
 // Column blocks along axis d-1 that lie inside one rank of both layouts.
 std::pair<size_t, int64_t> get_colblocks(tfft_plan p, int lin, int lout, int W) {
@@ -857,6 +888,42 @@ int tfft_plan_num_launches(tfft_plan p, int sign, int mode, int* n) {
   auto it = p->steps.find({sign, mode});
   if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
   *n = (int)it->second.size();
+  return TFFT_OK;
+}
+
+int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name, int name_len,
+                          int64_t* bytes) {
+  if (!p || !bytes || (name_len > 0 && !name)) return fail(TFFT_EINVAL, "NULL argument");
+  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length is not a product of 2, 3, 5 up to 4096");
+  auto it = p->steps.find({sign, mode});
+  if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
+  if (index < 0 || index >= (int)it->second.size()) return fail(TFFT_EINVAL, "launch index out of range");
+  const Step& s = it->second[index];
+  std::string nm;
+  int64_t elems = 0;
+  if (s.kind == S_BOX) {
+    nm = "box_copy";
+    const ExchangeBoxes* X = nullptr;
+    for (auto& kv : p->xbox_off)
+      for (int k = 0; k < 4; ++k)
+        if (kv.second[k] == s.box_off) {
+          const ExchangeBoxes& E = p->xboxes[kv.first];
+          const std::vector<BoxDesc>* v[4] = {&E.direct, &E.pack, &E.xchg, &E.unpack};
+          for (const BoxDesc& b : *v[k]) elems += b.ext[0] * b.ext[1] * b.ext[2] * b.ext[3];
+          X = &E;
+        }
+    (void)X;
+  } else {
+    const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
+    nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
+         (ap.E == 0 ? std::string("_generic") : "_E" + std::to_string(ap.E));
+    elems = p->nelems;
+  }
+  *bytes = 2 * elems * (int64_t)sizeof(float2);  // one read and one write of every element
+  if (name_len > 0) {
+    std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
   return TFFT_OK;
 }
 

@@ -231,6 +231,132 @@ __global__ void __launch_bounds__(512, 1) k_fft_strided(const StridedArgs a) {
   }
 }
 
+// ------------------------------------------------------------ generic lengths
+//
+// Lengths whose radices have no common register budget (those with all of
+// 2, 3 and 5 as factors, e.g. 60 or 120) keep the whole line in shared memory
+// between stages: two buffers, each stage reads one and writes the other,
+// every thread looping over the stage's L / R work items.
+
+template <int R>
+__device__ __forceinline__ void generic_stage(const float2* __restrict__ src, float2* __restrict__ dst,
+                                              int L, int Ns, int T, int jt, int stride, int cx,
+                                              const float2* __restrict__ tw) {
+  for (int j = jt; j < L / R; j += T) {
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = src[(j + r * (L / R)) * stride + cx];
+    if (Ns > 1) {
+      const int step = (j % Ns) * (L / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) x[r] = cmul(x[r], __ldg(&tw[r * step]));
+    }
+    Dft<R>::run(x);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[stockham_out_index(j, Ns, R, r) * stride + cx] = x[r];
+  }
+}
+
+// Runs every stage between the two shared buffers; returns the buffer that
+// holds the result.
+__device__ __forceinline__ float2* generic_fft(float2* b0, float2* b1, const AxisPlan& ap, int jt,
+                                               int stride, int cx, const float2* __restrict__ tw) {
+  int Ns = 1;
+  float2* src = b0;
+  float2* dst = b1;
+  for (int s = 0; s < ap.nst; ++s) {
+    const int R = stage_radix(ap.code, s);
+    switch (R) {
+      case 2: generic_stage<2>(src, dst, ap.L, Ns, ap.T, jt, stride, cx, tw); break;
+      case 3: generic_stage<3>(src, dst, ap.L, Ns, ap.T, jt, stride, cx, tw); break;
+      case 4: generic_stage<4>(src, dst, ap.L, Ns, ap.T, jt, stride, cx, tw); break;
+      case 5: generic_stage<5>(src, dst, ap.L, Ns, ap.T, jt, stride, cx, tw); break;
+      case 8: generic_stage<8>(src, dst, ap.L, Ns, ap.T, jt, stride, cx, tw); break;
+      case 16: generic_stage<16>(src, dst, ap.L, Ns, ap.T, jt, stride, cx, tw); break;
+      default: break;
+    }
+    __syncthreads();
+    float2* t = src;
+    src = dst;
+    dst = t;
+    Ns *= R;
+  }
+  return src;
+}
+
+__global__ void __launch_bounds__(512) k_fft_contig_generic(const ContigArgs a) {
+  extern __shared__ float2 smem[];
+  const int L = a.ap.L, T = a.ap.T;
+  const int jt = threadIdx.x, ly = threadIdx.y, B = blockDim.y;
+  float2* b0 = smem + (size_t)ly * L;
+  float2* b1 = smem + (size_t)(B + ly) * L;
+  const bool inv = a.sign > 0;
+  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
+    const int64_t line = base + ly;
+    const bool act = line < a.nlines;
+    __syncthreads();
+    for (int i = jt; i < L; i += T) {
+      float2 x = act ? a.in[line * L + i] : make_float2(0.f, 0.f);
+      if (inv) x.y = -x.y;
+      b0[i] = x;
+    }
+    __syncthreads();
+    const float2* res = generic_fft(b0, b1, a.ap, jt, 1, 0, a.tw);
+    for (int i = jt; i < L; i += T) {
+      float2 x = cscale(res[i], a.scale);
+      if (inv) x.y = -x.y;
+      if (act) a.out[line * L + i] = x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) k_fft_strided_generic(const StridedArgs a) {
+  extern __shared__ float2 smem[];
+  const int L = a.ap.L, T = a.ap.T, W = a.W;
+  const int cx = threadIdx.x, jt = threadIdx.y;
+  const int tid = jt * W + cx, nthr = W * T;
+  float2* b0 = smem;
+  float2* b1 = smem + (size_t)L * W;
+  int64_t* rin = reinterpret_cast<int64_t*>(smem + 2 * (size_t)L * W);
+  int64_t* rout = rin + L;
+  const bool inv = a.sign > 0;
+  const int64_t ntiles = a.nouter * a.ncolblocks;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t o = tile / a.ncolblocks;
+    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
+    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    __syncthreads();
+    for (int i = tid; i < L; i += nthr) {
+      int64_t g[MAXD];
+#pragma unroll
+      for (int m = 0; m < MAXD; ++m)
+        g[m] = (m == a.axis) ? (int64_t)i
+             : (m == a.d - 1) ? (int64_t)blk.x
+             : (m == a.oax0) ? go0
+             : (m == a.oax1) ? go1
+                             : 0;
+      rin[i] = layout_addr(a.lin, g[0], g[1], g[2], g[3]);
+      rout[i] = layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < L * W; idx += nthr) {
+      const int pos = idx / W, c = idx - (idx / W) * W;
+      float2 x = (c < blk.y) ? a.in[rin[pos] + c] : make_float2(0.f, 0.f);
+      if (inv) x.y = -x.y;
+      b0[idx] = x;
+    }
+    __syncthreads();
+    const float2* res = generic_fft(b0, b1, a.ap, jt, W, cx, a.tw);
+    for (int idx = tid; idx < L * W; idx += nthr) {
+      const int pos = idx / W, c = idx - (idx / W) * W;
+      float2 x = cscale(res[idx], a.scale);
+      if (inv) x.y = -x.y;
+      if (c < blk.y) a.out[rout[pos] + c] = x;
+    }
+  }
+}
+
 // ------------------------------------------------------------ box copy
 
 __global__ void __launch_bounds__(256) k_boxcopy(const BoxArgs a) {
@@ -333,6 +459,17 @@ bool kernel_supports_E(int E) {
 }
 
 cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
+  if (a.ap.E == 0) {
+    static cudaError_t attr = allow_smem(k_fft_contig_generic);
+    if (attr != cudaSuccess) return attr;
+    const int B = a.lines_per_cta;
+    const size_t smem = 2 * (size_t)B * a.ap.L * sizeof(float2);
+    int64_t grid = (a.nlines + B - 1) / B;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    if (grid < 1) return cudaSuccess;
+    k_fft_contig_generic<<<(unsigned)grid, dim3(a.ap.T, B), smem, s>>>(a);
+    return cudaGetLastError();
+  }
   switch (a.ap.E) {
 #define X(e) \
   case e:    \
@@ -345,6 +482,17 @@ cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
+  if (a.ap.E == 0) {
+    static cudaError_t attr = allow_smem(k_fft_strided_generic);
+    if (attr != cudaSuccess) return attr;
+    const int L = a.ap.L;
+    const size_t smem = 2 * (size_t)L * a.W * sizeof(float2) + 2 * (size_t)L * sizeof(int64_t);
+    int64_t grid = a.nouter * a.ncolblocks;
+    if (grid > kMaxGrid) grid = kMaxGrid;
+    if (grid < 1) return cudaSuccess;
+    k_fft_strided_generic<<<(unsigned)grid, dim3(a.W, a.ap.T), smem, s>>>(a);
+    return cudaGetLastError();
+  }
   switch (a.ap.E) {
 #define X(e) \
   case e:    \

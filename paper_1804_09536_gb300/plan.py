@@ -171,6 +171,16 @@ class Plan:
         call("tfft_partial", self._h, stage, axis, sign, _ptr(x), _stream_ptr(stream))
         return x
 
+    def launch_info(self, sign: int, mode: str = "fused"):
+        """[(kernel name, algorithmic bytes)] for every launch of one execute."""
+        out = []
+        for k in range(self.num_launches(sign, mode)):
+            buf = ctypes.create_string_buffer(64)
+            nb = ctypes.c_int64()
+            call("tfft_plan_launch_info", self._h, sign, _MODES[mode], k, buf, 64, ctypes.byref(nb))
+            out.append((buf.value.decode(), nb.value))
+        return out
+
     def set_launch_events(self, events):
         """Record torch.cuda.Event objects around every launch of later executes."""
         if not events:

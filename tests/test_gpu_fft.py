@@ -68,7 +68,7 @@ def test_forward_inverse_vs_oracle(cuda_device, shape, grid):
     assert np.array_equal(outs_b["fused"], outs_b["packed"])
 
 
-@pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((42, 40, 48), (3, 4))])
+@pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((40, 48, 60), (3, 4))])
 def test_round_trip_and_destroyed_input(cuda_device, shape, grid):
     """App. A: backward(forward(x)) = x; without a workspace the input is scratch."""
     from paper_1804_09536_gb300.plan import Plan
