@@ -239,6 +239,8 @@ struct AxisPlan {
   int T;           // threads per line = L / E
   int nst;         // number of radix stages
   uint64_t code;   // radix of stage s = (code >> 5 s) & 31
+  int spec;        // 1: a compile-time specialised kernel exists for this plan
+  int width;       // lines per CTA (contiguous) or tile width W (strided)
   int radix[MAXSTAGES];
 };
 

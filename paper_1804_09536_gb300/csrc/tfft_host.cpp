@@ -161,8 +161,10 @@ DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
 // `strided`: the line is one column of a W-wide tile of at most 512 threads,
 // so plans with at most 32 threads per line (W >= 16 columns) are preferred.
 bool make_axis_plan(int L, bool strided, AxisPlan& best) {
+  best.spec = 0;
+  best.width = 0;
   if (L == 1) {
-    best = AxisPlan{1, 1, 1, 0, 0, {}};
+    best = AxisPlan{1, 1, 1, 0, 0, 0, 1, {}};
     return true;
   }
   static const int Es[] = {8, 16, 4, 12, 20, 24, 10, 6, 15, 5, 3, 2};
@@ -244,6 +246,7 @@ bool make_axis_plan(int L, bool strided, AxisPlan& best) {
 }
 
 int strided_width(const AxisPlan& ap) {
+  if (ap.spec) return ap.width;
   int W = std::max(1, std::min(32, 512 / ap.T));
   // shared memory: L x W elements (two buffers for the generic kernel) + row tables
   const size_t budget = 200 * 1024 - 16 * (size_t)ap.L;
@@ -568,7 +571,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.nlines = s.nlines;
     a.ap = p->aplan[s.L];
     a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
-    a.lines_per_cta = std::max(1, 256 / a.ap.T);
+    a.lines_per_cta = a.ap.spec ? a.ap.width : std::max(1, 256 / a.ap.T);
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
     e = launch_contig(a, st);
@@ -730,6 +733,9 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
       p->transformable = false;
       continue;
     }
+    int width = 0;
+    if (spec_plan(L, false, p->nelems, ap, width)) ap.width = width;
+    if (spec_plan(L, true, p->nelems, aps, width)) aps.width = width;
     p->aplan[L] = ap;
     p->aplan_s[L] = aps;
     p->tw_off[L] = image_add(p, nullptr, (size_t)L * sizeof(float2));
@@ -916,7 +922,8 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
   } else {
     const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
     nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
-         (ap.E == 0 ? std::string("_generic") : "_E" + std::to_string(ap.E));
+         (ap.spec ? "_L" + std::to_string(ap.L) : ap.E == 0 ? std::string("_generic")
+                                                            : "_E" + std::to_string(ap.E));
     elems = p->nelems;
   }
   *bytes = 2 * elems * (int64_t)sizeof(float2);  // one read and one write of every element

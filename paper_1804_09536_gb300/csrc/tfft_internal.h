@@ -74,4 +74,10 @@ cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
 // Limits of the kernels, used by the planner.
 bool kernel_supports_E(int E);
 
+// Compile-time specialised passes (tfft_spec.cu): the plan of length L if one
+// exists (and the buffers fit 32-bit offsets), and their launchers.
+bool spec_plan(int L, bool strided, int64_t nelems, AxisPlan& ap, int& width);
+cudaError_t launch_contig_spec(const ContigArgs& a, cudaStream_t s);
+cudaError_t launch_strided_spec(const StridedArgs& a, cudaStream_t s);
+
 }  // namespace tfft

@@ -459,6 +459,7 @@ bool kernel_supports_E(int E) {
 }
 
 cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
+  if (a.ap.spec) return launch_contig_spec(a, s);
   if (a.ap.E == 0) {
     static cudaError_t attr = allow_smem(k_fft_contig_generic);
     if (attr != cudaSuccess) return attr;
@@ -482,6 +483,7 @@ cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
+  if (a.ap.spec) return launch_strided_spec(a, s);
   if (a.ap.E == 0) {
     static cudaError_t attr = allow_smem(k_fft_strided_generic);
     if (attr != cudaSuccess) return attr;

@@ -1,0 +1,317 @@
+// Compile-time specialised FFT passes for the axis lengths of the benchmark
+// workloads (32, 64, 96, 128, 160, 256, 512).  Same Stockham schedule as the
+// runtime-dispatched kernels (tfft_kernels.cu), but with the length, the
+// radix sequence, the threads per line and the tile width fixed at compile
+// time: every index, span and twiddle stride folds to a constant, the row
+// tables hold 32-bit offsets, and the register budget is known to ptxas.
+#include <type_traits>
+
+#include "tfft_internal.h"
+
+namespace tfft {
+
+namespace {
+
+template <int S, int... Rs>
+__host__ __device__ constexpr int radix_at() {
+  constexpr int r[] = {Rs...};
+  return r[S];
+}
+
+template <int S, int... Rs>
+__host__ __device__ constexpr int span_at() {
+  constexpr int r[] = {Rs...};
+  int p = 1;
+  for (int i = 0; i < S; ++i) p *= r[i];
+  return p;
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+// Twiddle (stage span Ns > 1) and size-R butterflies of a thread's work items.
+template <int L, int E, int R, int Ns>
+__device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2* __restrict__ tw) {
+  constexpr int T = L / E;
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    if constexpr (Ns > 1) {
+      const int j = jt + q * T;
+      const int step = (j % Ns) * (L / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], __ldg(&tw[r * step]));
+    }
+    Dft<R>::run(&v[q * R]);
+  }
+}
+
+// threadIdx re-read inside a loop body, opaque to the compiler: it keeps the
+// per-thread shared-memory addresses from being hoisted out of the tile loop
+// (and held in registers across it).
+__device__ __forceinline__ int opaque_tid_x() {
+  int v;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(v));
+  return v;
+}
+__device__ __forceinline__ int opaque_tid_y() {
+  int v;
+  asm volatile("mov.u32 %0, %%tid.y;" : "=r"(v));
+  return v;
+}
+
+// CTAs per SM the register budget is sized for: `target` resident threads
+// (half that for the 20-element plans, whose butterflies need more registers).
+__host__ __device__ constexpr int min_blocks(int E, int threads, int target) {
+  const int t = (E >= 20 ? target / 2 : target) / threads;
+  return t > 0 ? t : 1;
+}
+
+// Padded position inside a contiguous line: one spare slot every 8 elements
+// keeps the stride-R Stockham writes free of shared-memory bank conflicts.
+__device__ __forceinline__ int cpad(int pos) { return pos + (pos >> 3); }
+
+// ------------------------------------------------------------ contiguous lines
+
+template <int L, int E, int B, int... Rs>
+__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
+    k_contig_spec(const ContigArgs a) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  constexpr int LP = L + L / 8;
+  extern __shared__ float2 smem[];
+  const int ly = threadIdx.y;
+  float2* sl = smem + ly * LP;
+  const bool inv = a.sign > 0;
+  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
+    const int64_t line = base + ly;
+    const bool act = line < a.nlines;
+    const float2* src = a.in + line * L;
+    float2* dst = a.out + line * L;
+    const int jt = opaque_tid_x();
+    float2 v[E];
+    static_for<0, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float2 x = act ? src[jt + q * T + r * (L / R)] : make_float2(0.f, 0.f);
+            if (inv) x.y = -x.y;
+            v[q * R + r] = x;
+          }
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / Rp; ++q)
+#pragma unroll
+          for (int r = 0; r < Rp; ++r) sl[cpad(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = sl[cpad(jt + q * T + r * (L / R))];
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        float2 x = cscale(v[q * RL + r], a.scale);
+        if (inv) x.y = -x.y;
+        if (act) dst[jt + q * T + r * (L / RL)] = x;
+      }
+  }
+}
+
+// ------------------------------------------------------------ strided lines
+
+template <int L, int E, int W, int... Rs>
+__global__ void __launch_bounds__(W * (L / E), min_blocks(E, W * (L / E), 1024))
+    k_strided_spec(const StridedArgs a) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  extern __shared__ float2 smem[];
+  int* rin = reinterpret_cast<int*>(smem + L * W);
+  int* rout = rin + L;
+  const int cx = threadIdx.x;
+  const int tid = threadIdx.y * W + cx;
+  const bool inv = a.sign > 0;
+  const int64_t ntiles = a.nouter * a.ncolblocks;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t o = tile / a.ncolblocks;
+    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
+    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    __syncthreads();  // the previous tile is done with the row tables
+    for (int i = tid; i < L; i += W * T) {
+      int64_t g[MAXD];
+#pragma unroll
+      for (int m = 0; m < MAXD; ++m)
+        g[m] = (m == a.axis) ? (int64_t)i
+             : (m == a.d - 1) ? (int64_t)blk.x
+             : (m == a.oax0) ? go0
+             : (m == a.oax1) ? go1
+                             : 0;
+      rin[i] = (int)layout_addr(a.lin, g[0], g[1], g[2], g[3]);
+      rout[i] = (int)layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+    }
+    __syncthreads();
+    const bool act = cx < blk.y;
+    const int jt = opaque_tid_y();
+    float2 v[E];
+    static_for<0, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int pos = jt + q * T + r * (L / R);
+            float2 x = act ? a.in[rin[pos] + cx] : make_float2(0.f, 0.f);
+            if (inv) x.y = -x.y;
+            v[q * R + r] = x;
+          }
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / Rp; ++q)
+#pragma unroll
+          for (int r = 0; r < Rp; ++r)
+            smem[stockham_out_index(jt + q * T, Nsp, Rp, r) * W + cx] = v[q * Rp + r];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = smem[(jt + q * T + r * (L / R)) * W + cx];
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        float2 x = cscale(v[q * RL + r], a.scale);
+        if (inv) x.y = -x.y;
+        if (act) a.out[rout[jt + q * T + r * (L / RL)] + cx] = x;
+      }
+  }
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+constexpr int64_t kMaxGrid = 1 << 20;
+
+template <int L, int E, int B, int... Rs>
+cudaError_t run_contig(const ContigArgs& a, cudaStream_t s) {
+  static cudaError_t attr = allow_smem(k_contig_spec<L, E, B, Rs...>);
+  if (attr != cudaSuccess) return attr;
+  const size_t smem = (size_t)B * (L + L / 8) * sizeof(float2);
+  int64_t grid = (a.nlines + B - 1) / B;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaSuccess;
+  k_contig_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int L, int E, int W, int... Rs>
+cudaError_t run_strided(const StridedArgs& a, cudaStream_t s) {
+  static cudaError_t attr = allow_smem(k_strided_spec<L, E, W, Rs...>);
+  if (attr != cudaSuccess) return attr;
+  if (a.W != W) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)L * W * sizeof(float2) + 2 * (size_t)L * sizeof(int);
+  int64_t grid = a.nouter * a.ncolblocks;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaSuccess;
+  k_strided_spec<L, E, W, Rs...><<<(unsigned)grid, dim3(W, L / E), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// The table of specialisations: length; contiguous passes: elements per
+// thread and lines per CTA; strided passes: elements per thread and tile
+// width; radices.
+#define TFFT_SPECS(X)                       \
+  X(32, 8, 64, 8, 32, 8, 4)                 \
+  X(64, 8, 32, 8, 32, 8, 8)                 \
+  X(96, 12, 32, 12, 32, 4, 4, 3, 2)         \
+  X(128, 16, 32, 16, 32, 16, 8)             \
+  X(160, 20, 32, 20, 32, 5, 4, 4, 2)        \
+  X(256, 16, 16, 16, 32, 16, 16)            \
+  X(512, 8, 4, 16, 16, 8, 8, 8)
+
+struct SpecRow {
+  int L, EC, B, ES, W, nst, radix[6];
+};
+
+const SpecRow kSpecs[] = {
+#define X(L, EC, B, ES, W, ...) \
+  {L, EC, B, ES, W, (int)(sizeof((int[]){__VA_ARGS__}) / sizeof(int)), {__VA_ARGS__}},
+    TFFT_SPECS(X)
+#undef X
+};
+
+}  // namespace
+
+bool spec_plan(int L, bool strided, int64_t nelems, AxisPlan& ap, int& width) {
+  if (nelems >= (int64_t(1) << 31)) return false;  // 32-bit row offsets
+  for (const SpecRow& r : kSpecs) {
+    if (r.L != L) continue;
+    const int E = strided ? r.ES : r.EC;
+    ap.L = L;
+    ap.E = E;
+    ap.T = L / E;
+    ap.nst = r.nst;
+    ap.code = 0;
+    for (int s = 0; s < r.nst; ++s) {
+      ap.radix[s] = r.radix[s];
+      ap.code |= (uint64_t)r.radix[s] << (5 * s);
+    }
+    ap.spec = 1;
+    width = strided ? r.W : r.B;
+    return true;
+  }
+  return false;
+}
+
+cudaError_t launch_contig_spec(const ContigArgs& a, cudaStream_t s) {
+  switch (a.ap.L) {
+#define X(L, EC, B, ES, W, ...) \
+  case L:                       \
+    return run_contig<L, EC, B, __VA_ARGS__>(a, s);
+    TFFT_SPECS(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_strided_spec(const StridedArgs& a, cudaStream_t s) {
+  switch (a.ap.L) {
+#define X(L, EC, B, ES, W, ...) \
+  case L:                       \
+    return run_strided<L, ES, W, __VA_ARGS__>(a, s);
+    TFFT_SPECS(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace tfft
