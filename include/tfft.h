@@ -66,7 +66,11 @@ enum { TFFT_FORWARD = -1, TFFT_BACKWARD = +1 };
 enum { TFFT_C2C = 0, TFFT_R2C = 1 };
 enum { TFFT_FP32 = 0 };
 /* plan flags */
-enum { TFFT_NORM_FORWARD = 0, TFFT_NORM_BACKWARD = 4 };
+enum {
+  TFFT_NORM_FORWARD = 0,
+  TFFT_NORM_BACKWARD = 4,
+  TFFT_NO_TMA = 8 /* plain load/store passes even where the TMA-staged ones apply */
+};
 /* execution modes of tfft_execute */
 enum {
   TFFT_MODE_FUSED = 0,   /* redistributions fused into the FFT passes' loads/stores */
@@ -191,6 +195,14 @@ int tfft_plan_num_launches(tfft_plan plan, int sign, int mode, int *nlaunches);
  */
 int tfft_plan_launch_info(tfft_plan plan, int sign, int mode, int index, char *name,
                           int name_len, int64_t *bytes);
+
+/*
+ * Device status word of the plan's state buffer: bit 0 (value 1) is set when
+ * a kernel gave up on a bounded wait for one of its own asynchronous copies
+ * (nothing else writes it).  Synchronises `stream`; reset != 0 clears the
+ * word afterwards.
+ */
+int tfft_plan_device_status(tfft_plan plan, int *status, int reset, void *stream);
 
 /*
  * Timing hook: record caller-created CUDA events (cudaEvent_t as void*) on

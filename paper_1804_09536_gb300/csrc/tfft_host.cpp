@@ -9,6 +9,9 @@
 #include <tuple>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "tfft.h"
 #include "tfft_internal.h"
 
@@ -67,6 +70,9 @@ struct Step {
   int nboxes = 0;
   int64_t max_rows = 0;
   int vec2 = 0;
+  // TMA-staged strided pass: tile geometry of the input and output layouts
+  bool tma = false;
+  TmaGeo gin{}, gout{};
 };
 
 struct ExchangeBoxes {  // one adjacent-stage exchange
@@ -85,6 +91,7 @@ struct tfft_plan_s {
   int nranks = 1;
   int64_t nelems = 0;  // complex elements of every stage buffer
   bool transformable = true;  // every axis length has an FFT plan
+  bool use_tma = true;        // TMA-staged passes where their conditions hold
   std::vector<LayoutH> st;
   std::map<int, AxisPlan> aplan;   // contiguous-line passes
   std::map<int, AxisPlan> aplan_s; // strided passes
@@ -162,9 +169,10 @@ DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
 // so plans with at most 32 threads per line (W >= 16 columns) are preferred.
 bool make_axis_plan(int L, bool strided, AxisPlan& best) {
   best.spec = 0;
+  best.tma = 0;
   best.width = 0;
   if (L == 1) {
-    best = AxisPlan{1, 1, 1, 0, 0, 0, 1, {}};
+    best = AxisPlan{1, 1, 1, 0, 0, 0, 0, 1, {}};
     return true;
   }
   static const int Es[] = {8, 16, 4, 12, 20, 24, 10, 6, 15, 5, 3, 2};
@@ -449,6 +457,71 @@ Step box_step(tfft_plan p, const std::vector<BoxDesc>& boxes, size_t off) {
   return s;
 }
 
+// The 5-D view of a stage layout used by the TMA passes exists when d == 3,
+// every cut axis splits evenly, and each rank's innermost extent is a
+// multiple of the tile width (every tile starts on a 16-byte boundary).
+bool tma_geo(tfft_plan p, int stage, int axis, int W, TmaGeo& G) {
+  if (p->d != 3 || p->g < 1 || p->g > 2) return false;
+  const LayoutH& S = p->st[stage];
+  const int L = (int)p->cshape[axis];
+  for (int m = 0; m < 3; ++m) {
+    G.cut[m] = S.owner[m] >= 0 ? 1 : 0;
+    const int64_t M = G.cut[m] ? p->grid[S.owner[m]] : 1;
+    if (p->cshape[m] % M) return false;
+    G.n[m] = (int)(p->cshape[m] / M);
+    G.rdim[m] = G.cut[m] ? 3 + (p->g - 1 - S.owner[m]) : 0;
+  }
+  if (G.n[2] % W != 0 || (W & 1)) return false;
+  if (G.cut[axis]) {
+    if (G.n[axis] > 256 || p->grid[S.owner[axis]] > 256) return false;
+    G.nops = 1;
+    G.rows_per_op = L;
+  } else {
+    G.rows_per_op = L < 256 ? L : 256;
+    if (L % G.rows_per_op) return false;
+    G.nops = L / G.rows_per_op;
+  }
+  return true;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+
+// Tensor map of a whole stage buffer as [D4][D3][n0][n1][n2] complex64
+// elements, with the box of one TMA op of a tile along `axis`.
+bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void* base, CUtensorMap* map) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int64_t local = (int64_t)G.n[0] * G.n[1] * G.n[2];
+  const cuuint64_t D3 = p->g >= 1 ? (cuuint64_t)p->grid[p->g - 1] : 1;
+  const cuuint64_t D4 = p->g == 2 ? (cuuint64_t)p->grid[0] : 1;
+  cuuint64_t dims[5] = {(cuuint64_t)G.n[2], (cuuint64_t)G.n[1], (cuuint64_t)G.n[0], D3, D4};
+  cuuint64_t strides[4] = {(cuuint64_t)G.n[2] * 8, (cuuint64_t)G.n[1] * G.n[2] * 8, (cuuint64_t)local * 8,
+                           (cuuint64_t)local * 8 * D3};
+  cuuint32_t box[5] = {(cuuint32_t)W, 1, 1, 1, 1};
+  if (G.cut[axis]) {
+    box[2 - axis] = (cuuint32_t)G.n[axis];                             // local rows
+    box[G.rdim[axis]] = (cuuint32_t)(p->cshape[axis] / G.n[axis]);     // every rank of the subgroup
+  } else {
+    box[2 - axis] = (cuuint32_t)G.rows_per_op;
+  }
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
   Step s;
   s.sign = sign;
@@ -468,6 +541,9 @@ Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
     auto cb = get_colblocks(p, lin, lout, s.W);
     s.cb_off = cb.first;
     s.ncb = cb.second;
+    int Wt = 0;
+    s.tma = p->use_tma && ap.spec && tma_width(s.L, Wt) && Wt == s.W &&
+            tma_geo(p, lin, axis, s.W, s.gin) && tma_geo(p, lout, axis, s.W, s.gout);
   }
   return s;
 }
@@ -574,7 +650,11 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.lines_per_cta = a.ap.spec ? a.ap.width : std::max(1, 256 / a.ap.T);
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
-    e = launch_contig(a, st);
+    a.status = reinterpret_cast<int*>(p->d_state);
+    if (a.ap.tma && p->use_tma)
+      e = launch_contig_tma(a, st);
+    else
+      e = launch_contig(a, st);
   } else if (s.kind == S_STRIDED) {
     StridedArgs a;
     a.in = in;
@@ -601,7 +681,16 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.W = s.W;
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
-    e = launch_strided(a, st);
+    a.status = reinterpret_cast<int*>(p->d_state);
+    bool done = false;
+    if (s.tma) {
+      alignas(64) CUtensorMap ti, to;
+      if (encode_stage_map(p, s.gin, s.axis, s.W, in, &ti) && encode_stage_map(p, s.gout, s.axis, s.W, out, &to)) {
+        e = launch_strided_tma(a, s.gin, s.gout, &ti, &to, st);
+        done = true;
+      }
+    }
+    if (!done) e = launch_strided(a, st);
   } else {
     BoxArgs a;
     a.in = in;
@@ -681,7 +770,7 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
   if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
   if (kind == TFFT_R2C) return fail(TFFT_EUNSUPPORTED, "real-to-complex plans are not built yet");
   if (precision != TFFT_FP32) return fail(TFFT_EUNSUPPORTED, "precision must be TFFT_FP32");
-  if (flags & ~TFFT_NORM_BACKWARD) return fail(TFFT_EINVAL, "unknown flag bits");
+  if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA)) return fail(TFFT_EINVAL, "unknown flag bits");
   auto p = new tfft_plan_s();
   p->d = ndims;
   p->g = grid_ndims;
@@ -717,6 +806,8 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     s *= grid[i];
   }
   // stage layouts and their rank offset tables
+  p->use_tma = !(flags & TFFT_NO_TMA);
+  image_add(p, nullptr, 256);  // device status word(s) at offset 0
   p->st.resize(p->g + 1);
   for (int s = 0; s <= p->g; ++s) {
     build_layout(p, p->cshape, s, p->st[s]);
@@ -735,6 +826,11 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     }
     int width = 0;
     if (spec_plan(L, false, p->nelems, ap, width)) ap.width = width;
+    int Ec = 0, Bc = 0;
+    if (p->use_tma && ap.spec && tma_contig_plan(L, Ec, Bc) && Ec == ap.E) {
+      ap.width = Bc;
+      ap.tma = 1;
+    }
     if (spec_plan(L, true, p->nelems, aps, width)) aps.width = width;
     p->aplan[L] = ap;
     p->aplan_s[L] = aps;
@@ -921,7 +1017,8 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
     (void)X;
   } else {
     const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
-    nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
+    const bool tma = (s.kind == S_CONTIG) ? (ap.tma && p->use_tma) : s.tma;
+    nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") + (tma ? "_tma" : "") +
          (ap.spec ? "_L" + std::to_string(ap.L) : ap.E == 0 ? std::string("_generic")
                                                             : "_E" + std::to_string(ap.E));
     elems = p->nelems;
@@ -931,6 +1028,23 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
     std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
     name[name_len - 1] = 0;
   }
+  return TFFT_OK;
+}
+
+int tfft_plan_device_status(tfft_plan p, int* status, int reset, void* stream) {
+  if (!p || !status) return fail(TFFT_EINVAL, "NULL argument");
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, p->d_state, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && reset) {
+    const int zero = 0;
+    e = cudaMemcpyAsync(p->d_state, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+  *status = v;
   return TFFT_OK;
 }
 

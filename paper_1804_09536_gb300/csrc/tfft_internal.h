@@ -7,6 +7,10 @@
 
 namespace tfft {
 
+// Bits of the plan's device status word (set by kernels, read by
+// tfft_plan_device_status()).
+constexpr int TFFT_DEVICE_ETIMEOUT = 1;  // a bounded wait on a copy expired
+
 // Batched 1-D FFT of contiguous lines (the axis held whole and innermost,
 // Eq. pencil0 / slab0): line l of the buffer is elements [l L, (l + 1) L).
 struct ContigArgs {
@@ -18,6 +22,7 @@ struct ContigArgs {
   int lines_per_cta;
   int sign;
   float scale;
+  int* status;       // device status word
 };
 
 // 1-D FFT along axis `axis` < d - 1 with the redistribution fused into the
@@ -43,6 +48,20 @@ struct StridedArgs {
   int W;                  // block width (blockDim.x)
   int sign;
   float scale;
+  int* status;            // device status word
+};
+
+// Tile geometry of one stage layout seen as the 5-D array
+// [rank dim 4][rank dim 3][n0][n1][n2] (d = 3, equal blocks on every rank):
+// for each axis m, whether it is cut, its local extent and the 5-D dimension
+// of the rank coordinate that cuts it; a tile's rows along the FFT axis are
+// loaded / stored in `nops` boxes of `rows_per_op` rows.
+struct TmaGeo {
+  int cut[3];
+  int n[3];
+  int rdim[3];
+  int nops;
+  int rows_per_op;
 };
 
 // Copy of rectangular boxes: each box has up to MAXD extents, a source and a
@@ -79,5 +98,12 @@ bool kernel_supports_E(int E);
 bool spec_plan(int L, bool strided, int64_t nelems, AxisPlan& ap, int& width);
 cudaError_t launch_contig_spec(const ContigArgs& a, cudaStream_t s);
 cudaError_t launch_strided_spec(const StridedArgs& a, cudaStream_t s);
+
+// TMA-staged passes (tfft_tma.cu).  tmap_* point to host CUtensorMap objects.
+bool tma_width(int L, int& W);
+bool tma_contig_plan(int L, int& E, int& B);
+cudaError_t launch_strided_tma(const StridedArgs& a, const TmaGeo& gin, const TmaGeo& gout,
+                               const void* tmap_in, const void* tmap_out, cudaStream_t s);
+cudaError_t launch_contig_tma(const ContigArgs& a, cudaStream_t s);
 
 }  // namespace tfft

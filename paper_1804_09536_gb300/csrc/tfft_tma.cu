@@ -1,0 +1,522 @@
+// TMA-staged FFT passes (sm_103a).
+//
+// Strided passes with the redistribution fused in: when every virtual rank of
+// the input and output stage holds an equal block (the decomposition divides
+// every cut axis), a stage buffer is a regular 5-D array
+// [rank dim][rank dim][n0][n1][n2] and one tensor map describes it.  A tile
+// (all L rows of the FFT axis x W columns of the innermost axis) is then one
+// or two cp.async.bulk.tensor copies -- the box spans the local rows and the
+// rank coordinate of the subgroup that cuts the FFT axis, so the gather of
+// the line from its M owners (Alg. 3's subarray boxes) is done by the copy
+// engine -- and the result goes back the same way into the output stage,
+// whose box spans the other subgroup (the scatter).  Tiles are
+// buffered three deep: the copy of tile i+1 runs while tile i is
+// transformed and the store of tile i-1 drains.
+//
+// Contiguous passes stream B whole lines per tile with 1-D bulk copies, also
+// double-buffered.
+//
+// Every wait on an mbarrier is bounded: on expiry the CTA records
+// TFFT_DEVICE_ETIMEOUT in the plan's status word and leaves.
+#include <cuda.h>
+
+#include <type_traits>
+
+#include "tfft_internal.h"
+
+namespace tfft {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            const int (&c)[5]) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c[0]), "r"(c[1]), "r"(c[2]),
+      "r"(c[3]), "r"(c[4])
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, const void* src, const int (&c)[5]) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+template <int S, int... Rs>
+__host__ __device__ constexpr int radix_at() {
+  constexpr int r[] = {Rs...};
+  return r[S];
+}
+
+template <int S, int... Rs>
+__host__ __device__ constexpr int span_at() {
+  constexpr int r[] = {Rs...};
+  int p = 1;
+  for (int i = 0; i < S; ++i) p *= r[i];
+  return p;
+}
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
+  }
+}
+
+template <int L, int E, int R, int Ns>
+__device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2* __restrict__ tw) {
+  constexpr int T = L / E;
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    if constexpr (Ns > 1) {
+      const int j = jt + q * T;
+      const int step = (j % Ns) * (L / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], __ldg(&tw[r * step]));
+    }
+    Dft<R>::run(&v[q * R]);
+  }
+}
+
+__device__ __forceinline__ int opaque_tid_x() {
+  int v;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(v));
+  return v;
+}
+__device__ __forceinline__ int opaque_tid_y() {
+  int v;
+  asm volatile("mov.u32 %0, %%tid.y;" : "=r"(v));
+  return v;
+}
+
+constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait is declared stuck
+
+// Coordinates of op k of a tile in one stage layout (see TmaGeo).
+__device__ __forceinline__ void tile_coords(const TmaGeo& G, int axis, int k, int64_t col, int64_t gt,
+                                            int tax, int (&c)[5]) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) c[i] = 0;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    int64_t g = (m == axis) ? (int64_t)k * G.rows_per_op : (m == 2) ? col : (m == tax) ? gt : 0;
+    if (G.cut[m]) {
+      if (m == axis) g = 0;  // the box spans every rank of the subgroup
+      const int64_t p = g / G.n[m];
+      c[2 - m] = (int)(g - p * G.n[m]);
+      c[G.rdim[m]] = (int)p;
+    } else {
+      c[2 - m] = (int)g;
+    }
+  }
+}
+
+// ------------------------------------------------------------ strided, TMA
+
+template <int L, int E, int W, int... Rs>
+__global__ void __launch_bounds__(W * (L / E), 1)
+    k_strided_tma(const StridedArgs a, const TmaGeo gin, const TmaGeo gout,
+                  const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  constexpr int WP = (W % 16 == 0) ? W : W + 1;  // exchange pitch (bank-conflict padding)
+  constexpr int BUF = L * (W + 1);
+  extern __shared__ __align__(128) float2 smem[];
+  // three tile buffers: tile i is transformed in buffer i % 3 while tile i+1
+  // is loaded into the next one and the store of tile i-1 still reads its own
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 3 * BUF);
+  const int cx = threadIdx.x;
+  const int tid = threadIdx.y * W + cx;
+  const bool inv = a.sign > 0;
+  const int64_t ntiles = a.nouter * a.ncolblocks;
+  const int tax = (a.oax0 >= 0) ? a.oax0 : -1;  // the outer axis (d == 3)
+  const uint32_t tile_bytes = (uint32_t)(L * W * sizeof(float2));
+
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b) mbar_init(&bars[b], 1);
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  __syncthreads();
+
+  auto issue_load = [&](int64_t tile, float2* dst, uint64_t* bar) {
+    const int64_t o = tile / a.ncolblocks;
+    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+    mbar_expect_tx(bar, tile_bytes);
+    for (int k = 0; k < gin.nops; ++k) {
+      int c[5];
+      tile_coords(gin, a.axis, k, blk.x, o, tax, c);
+      tma_load_5d(dst + (size_t)k * gin.rows_per_op * W, &tin, bar, c);
+    }
+  };
+
+  int64_t tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue_load(tile, smem, &bars[0]);
+  int it = 0, b = 0;  // b = it % 3
+  for (; tile < ntiles; tile += gridDim.x, ++it, b = (b == 2) ? 0 : b + 1) {
+    float2* cur = smem + b * BUF;
+    const int bn = (b == 2) ? 0 : b + 1;
+    const int64_t next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) {
+      bulk_wait_read<1>();  // the store of tile it-2 has finished reading buffer bn
+      fence_proxy_async();
+      issue_load(next, smem + bn * BUF, &bars[bn]);
+    }
+    bool ok = true;
+    if (!mbar_wait(&bars[b], (it / 3) & 1, kWaitLimit)) ok = false;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
+        // give the copies still in flight (this tile's and the next one's) a
+        // bounded chance to land before the CTA leaves
+        mbar_wait(&bars[b], (it / 3) & 1, kWaitLimit);
+        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / 3) & 1, kWaitLimit);
+      }
+      break;
+    }
+    const int jt = opaque_tid_y();
+    float2 v[E];
+    static_for<0, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float2 x = cur[(jt + q * T + r * (L / R)) * W + cx];
+            if (inv) x.y = -x.y;
+            v[q * R + r] = x;
+          }
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / Rp; ++q)
+#pragma unroll
+          for (int r = 0; r < Rp; ++r)
+            cur[stockham_out_index(jt + q * T, Nsp, Rp, r) * WP + cx] = v[q * Rp + r];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = cur[(jt + q * T + r * (L / R)) * WP + cx];
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        float2 x = cscale(v[q * RL + r], a.scale);
+        if (inv) x.y = -x.y;
+        cur[(jt + q * T + r * (L / RL)) * W + cx] = x;
+      }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      const int64_t o = tile / a.ncolblocks;
+      const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+      for (int k = 0; k < gout.nops; ++k) {
+        int c[5];
+        tile_coords(gout, a.axis, k, blk.x, o, tax, c);
+        tma_store_5d(&tout, cur + (size_t)k * gout.rows_per_op * W, c);
+      }
+      bulk_commit();
+    }
+  }
+  if (tid == 0) bulk_wait_all();
+}
+
+// ------------------------------------------------------------ contiguous, bulk copies
+
+template <int L, int E, int B, int... Rs>
+__global__ void __launch_bounds__((L / E) * B, 1)
+    k_contig_tma(const ContigArgs a) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  constexpr int LP = L + L / 8;
+  extern __shared__ __align__(128) float2 smem[];
+  float2* in0 = smem;
+  float2* in1 = smem + B * L;
+  float2* xch = smem + 2 * B * L;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * B * L + B * LP);
+  const int ly = threadIdx.y;
+  const int tid = ly * T + threadIdx.x;
+  const bool inv = a.sign > 0;
+  const int64_t ntiles = (a.nlines + B - 1) / B;
+  float2* sl = xch + ly * LP;
+
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+    fence_proxy_async();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t tile, float2* dst, uint64_t* bar) {
+    const int64_t first = tile * B;
+    const int64_t nl = (a.nlines - first < B) ? (a.nlines - first) : B;
+    const uint32_t bytes = (uint32_t)(nl * L * sizeof(float2));
+    mbar_expect_tx(bar, bytes);
+    bulk_load(dst, a.in + first * L, bytes, bar);
+  };
+  int64_t tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile, in0, &bars[0]);
+  int it = 0;
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    float2* cur = (it & 1) ? in1 : in0;
+    float2* nxt = (it & 1) ? in0 : in1;
+    const int64_t next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) {
+      fence_proxy_async();
+      issue(next, nxt, &bars[(it + 1) & 1]);
+    }
+    bool ok = true;
+    if (!mbar_wait(&bars[it & 1], (it >> 1) & 1, kWaitLimit)) ok = false;
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
+        mbar_wait(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
+        if (next < ntiles) mbar_wait(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kWaitLimit);
+      }
+      break;
+    }
+    const int64_t line = tile * B + ly;
+    const bool act = line < a.nlines;
+    const int jt = opaque_tid_x();
+    const float2* src = cur + ly * L;
+    float2* dst = a.out + line * L;
+    float2 v[E];
+    static_for<0, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float2 x = src[jt + q * T + r * (L / R)];
+            if (inv) x.y = -x.y;
+            v[q * R + r] = x;
+          }
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / Rp; ++q)
+#pragma unroll
+          for (int r = 0; r < Rp; ++r) {
+            const int pos = stockham_out_index(jt + q * T, Nsp, Rp, r);
+            sl[pos + (pos >> 3)] = v[q * Rp + r];
+          }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int pos = jt + q * T + r * (L / R);
+            v[q * R + r] = sl[pos + (pos >> 3)];
+          }
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        float2 x = cscale(v[q * RL + r], a.scale);
+        if (inv) x.y = -x.y;
+        if (act) dst[jt + q * T + r * (L / RL)] = x;
+      }
+    __syncthreads();  // every thread is done with `cur` before it is refilled
+  }
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+int sm_count() {
+  static int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
+template <class K>
+int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t g = (int64_t)per_sm * sm_count();
+  return ntiles < g ? ntiles : g;
+}
+
+template <int L, int E, int W, int... Rs>
+cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo& go, const CUtensorMap& ti,
+                            const CUtensorMap& to, cudaStream_t s) {
+  auto kern = k_strided_tma<L, E, W, Rs...>;
+  static cudaError_t attr = allow_smem(kern);
+  if (attr != cudaSuccess) return attr;
+  if (a.W != W) return cudaErrorInvalidValue;
+  const size_t smem = 3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t);
+  const int threads = W * (L / E);
+  static const int64_t slots = persistent_grid(kern, threads, smem, int64_t(1) << 40);
+  const int64_t ntiles = a.nouter * a.ncolblocks;
+  const int64_t grid = ntiles < slots ? ntiles : slots;
+  if (grid < 1) return cudaSuccess;
+  kern<<<(unsigned)grid, dim3(W, L / E), smem, s>>>(a, gi, go, ti, to);
+  return cudaGetLastError();
+}
+
+template <int L, int E, int B, int... Rs>
+cudaError_t run_contig_tma(const ContigArgs& a, cudaStream_t s) {
+  auto kern = k_contig_tma<L, E, B, Rs...>;
+  static cudaError_t attr = allow_smem(kern);
+  if (attr != cudaSuccess) return attr;
+  const size_t smem = (2 * (size_t)B * L + (size_t)B * (L + L / 8)) * sizeof(float2) + 2 * sizeof(uint64_t);
+  const int threads = (L / E) * B;
+  static const int64_t slots = persistent_grid(kern, threads, smem, int64_t(1) << 40);
+  const int64_t ntiles = (a.nlines + B - 1) / B;
+  const int64_t grid = ntiles < slots ? ntiles : slots;
+  if (grid < 1) return cudaSuccess;
+  kern<<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Lengths with a TMA variant: L, strided elements per thread and tile width,
+// contiguous elements per thread and lines per tile, radices.
+#define TFFT_TMA_SPECS(X)                 \
+  X(64, 8, 32, 8, 32, 8, 8)               \
+  X(128, 16, 32, 16, 16, 16, 8)           \
+  X(256, 16, 32, 16, 8, 16, 16)           \
+  X(512, 16, 16, 8, 4, 8, 8, 8)
+
+}  // namespace
+
+bool tma_width(int L, int& W) {
+  switch (L) {
+#define X(LL, ES, WW, EC, BB, ...) \
+  case LL:                         \
+    W = WW;                        \
+    return true;
+    TFFT_TMA_SPECS(X)
+#undef X
+    default:
+      return false;
+  }
+}
+
+bool tma_contig_plan(int L, int& E, int& B) {
+  switch (L) {
+#define X(LL, ES, WW, EC, BB, ...) \
+  case LL:                         \
+    E = EC;                        \
+    B = BB;                        \
+    return true;
+    TFFT_TMA_SPECS(X)
+#undef X
+    default:
+      return false;
+  }
+}
+
+cudaError_t launch_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo& go, const void* tmap_in,
+                               const void* tmap_out, cudaStream_t s) {
+  const CUtensorMap& ti = *static_cast<const CUtensorMap*>(tmap_in);
+  const CUtensorMap& to = *static_cast<const CUtensorMap*>(tmap_out);
+  switch (a.ap.L) {
+#define X(LL, ES, WW, EC, BB, ...) \
+  case LL:                         \
+    return run_strided_tma<LL, ES, WW, __VA_ARGS__>(a, gi, go, ti, to, s);
+    TFFT_TMA_SPECS(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_contig_tma(const ContigArgs& a, cudaStream_t s) {
+  switch (a.ap.L) {
+#define X(LL, ES, WW, EC, BB, ...) \
+  case LL:                         \
+    return run_contig_tma<LL, EC, BB, __VA_ARGS__>(a, s);
+    TFFT_TMA_SPECS(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace tfft

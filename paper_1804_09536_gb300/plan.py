@@ -38,12 +38,14 @@ class Plan:
     """
 
     def __init__(self, shape, grid, kind: str = "c2c", norm: str = "forward", device=None,
-                 bind: bool = True):
+                 bind: bool = True, tma: bool = True):
         self.shape = tuple(int(n) for n in shape)
         self.grid = tuple(int(m) for m in grid)
         self.kind = kind
         kind_id = {"c2c": _lib.TFFT_C2C, "r2c": _lib.TFFT_R2C}[kind]
         flags = {"forward": _lib.TFFT_NORM_FORWARD, "backward": _lib.TFFT_NORM_BACKWARD}[norm]
+        if not tma:
+            flags |= _lib.TFFT_NO_TMA
         h = ctypes.c_void_p()
         shp = (ctypes.c_int64 * len(self.shape))(*self.shape)
         grd = (ctypes.c_int * max(1, len(self.grid)))(*(self.grid or (1,)))
@@ -170,6 +172,12 @@ class Plan:
     def partial(self, stage: int, axis: int, sign: int, x: torch.Tensor, stream=None) -> torch.Tensor:
         call("tfft_partial", self._h, stage, axis, sign, _ptr(x), _stream_ptr(stream))
         return x
+
+    def device_status(self, reset: bool = False, stream=None) -> int:
+        """Status word written by the kernels (1 = a bounded wait expired)."""
+        v = ctypes.c_int()
+        call("tfft_plan_device_status", self._h, ctypes.byref(v), int(reset), _stream_ptr(stream))
+        return v.value
 
     def launch_info(self, sign: int, mode: str = "fused"):
         """[(kernel name, algorithmic bytes)] for every launch of one execute."""
