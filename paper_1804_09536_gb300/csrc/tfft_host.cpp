@@ -1,6 +1,7 @@
 // Host side of the C ABI (include/tfft.h): plan construction on the virtual
 // process grid, state image, pass lists and launches.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -50,7 +51,7 @@ struct LayoutH {
   size_t state_off = 0;  // rank offset table in the state image (bytes)
 };
 
-enum StepKind { S_CONTIG, S_STRIDED, S_BOX };
+enum StepKind { S_CONTIG, S_STRIDED, S_BOX, S_REAL };
 enum BufId { BUF_IN, BUF_OUT, BUF_W0, BUF_W1 };
 
 struct Step {
@@ -70,8 +71,12 @@ struct Step {
   int nboxes = 0;
   int64_t max_rows = 0;
   int vec2 = 0;
-  // TMA-staged strided pass: tile geometry of the input and output layouts
+  // TMA-staged strided pass: variant, its column blocks and the tile
+  // geometry of the input and output layouts
   bool tma = false;
+  int tma_E = 0, tma_W = 0;
+  size_t tma_cb_off = 0;
+  int64_t tma_ncb = 0;
   TmaGeo gin{}, gout{};
 };
 
@@ -90,6 +95,9 @@ struct tfft_plan_s {
   int64_t rstride[MAXG] = {0, 0, 0};
   int nranks = 1;
   int64_t nelems = 0;  // complex elements of every stage buffer
+  int64_t nreal = 0;   // real elements of the real stage-0 buffer (R2C)
+  LayoutH real0;       // real stage-0 layout (R2C)
+  AxisPlan rplan{};    // complex FFT of half the innermost length (R2C)
   bool transformable = true;  // every axis length has an FFT plan
   bool use_tma = true;        // TMA-staged passes where their conditions hold
   std::vector<LayoutH> st;
@@ -522,6 +530,30 @@ bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void*
   return r == CUDA_SUCCESS;
 }
 
+// Tile width (and optionally elements per thread) requested for the strided
+// TMA pass of length L by the environment, TFFT_TMA_W="512:8:16,256:32"
+// (used when tuning); 0 when not given.
+int tuned_width(int L, int* E = nullptr) {
+  if (E) *E = 0;
+  const char* env = std::getenv("TFFT_TMA_W");
+  if (!env) return 0;
+  std::string v(env);
+  size_t pos = 0;
+  while (pos < v.size()) {
+    size_t comma = v.find(',', pos);
+    std::string item = v.substr(pos, comma == std::string::npos ? std::string::npos : comma - pos);
+    size_t colon = item.find(':');
+    if (colon != std::string::npos && std::atoi(item.substr(0, colon).c_str()) == L) {
+      size_t colon2 = item.find(':', colon + 1);
+      if (E && colon2 != std::string::npos) *E = std::atoi(item.substr(colon2 + 1).c_str());
+      return std::atoi(item.substr(colon + 1).c_str());
+    }
+    if (comma == std::string::npos) break;
+    pos = comma + 1;
+  }
+  return 0;
+}
+
 Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
   Step s;
   s.sign = sign;
@@ -541,10 +573,33 @@ Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
     auto cb = get_colblocks(p, lin, lout, s.W);
     s.cb_off = cb.first;
     s.ncb = cb.second;
-    int Wt = 0;
-    s.tma = p->use_tma && ap.spec && tma_width(s.L, Wt) && Wt == s.W &&
-            tma_geo(p, lin, axis, s.W, s.gin) && tma_geo(p, lout, axis, s.W, s.gout);
+    int Et = 0, Wt = 0, wantE = 0;
+    const int wantW = tuned_width(s.L, &wantE);
+    s.tma = p->use_tma && ap.spec && tma_strided_variant(s.L, wantW, wantE, Et, Wt) &&
+            tma_geo(p, lin, axis, Wt, s.gin) && tma_geo(p, lout, axis, Wt, s.gout);
+    if (s.tma) {
+      s.tma_E = Et;
+      s.tma_W = Wt;
+      auto cbt = get_colblocks(p, lin, lout, Wt);
+      s.tma_cb_off = cbt.first;
+      s.tma_ncb = cbt.second;
+    }
   }
+  return s;
+}
+
+// The pass along the innermost axis: a complex FFT of contiguous lines, or
+// for a real-to-complex plan the r2c (forward) / c2r (backward) pass between
+// the real and the complex stage-0 buffers.
+Step last_axis_step(tfft_plan p, int sign) {
+  if (p->kind != TFFT_R2C) return fft_step(p, p->d - 1, 0, 0, sign);
+  Step s;
+  s.kind = S_REAL;
+  s.sign = sign;
+  s.axis = p->d - 1;
+  s.inplace_ok = false;
+  s.L = p->rplan.L;
+  s.nlines = p->nreal / (2 * (int64_t)p->rplan.L);
   return s;
 }
 
@@ -566,15 +621,15 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
   std::vector<Step> v;
   if (mode == TFFT_MODE_FUSED) {
     if (sign == TFFT_FORWARD) {
-      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+      v.push_back(last_axis_step(p, sign));
       for (int a = d - 2; a >= 0; --a) v.push_back(fft_step(p, a, a == d - 2 ? 0 : g, g, sign));
     } else {
       for (int a = 0; a <= d - 2; ++a) v.push_back(fft_step(p, a, g, a == d - 2 ? 0 : g, sign));
-      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+      v.push_back(last_axis_step(p, sign));
     }
   } else {
     if (sign == TFFT_FORWARD) {
-      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+      v.push_back(last_axis_step(p, sign));
       for (int a = d - 2; a >= g; --a) v.push_back(fft_step(p, a, 0, 0, sign));
       for (int s = 1; s <= g; ++s) {
         add_exchange_steps(p, v, s - 1, s, mode);
@@ -586,7 +641,7 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
         add_exchange_steps(p, v, s, s - 1, mode);
       }
       for (int a = g; a <= d - 2; ++a) v.push_back(fft_step(p, a, 0, 0, sign));
-      v.push_back(fft_step(p, d - 1, 0, 0, sign));
+      v.push_back(last_axis_step(p, sign));
     }
   }
   // normalisation on the last FFT pass of the scaled direction
@@ -595,7 +650,7 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
     for (int k = (int)v.size() - 1; k >= 0; --k)
       if (v[k].kind != S_BOX) {
         v[k].scaled = true;
-        v[k].scale_value = 1.0 / (double)p->nelems;
+        v[k].scale_value = 1.0 / (double)(p->kind == TFFT_R2C ? p->nreal : p->nelems);
         break;
       }
   }
@@ -685,12 +740,31 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     bool done = false;
     if (s.tma) {
       alignas(64) CUtensorMap ti, to;
-      if (encode_stage_map(p, s.gin, s.axis, s.W, in, &ti) && encode_stage_map(p, s.gout, s.axis, s.W, out, &to)) {
-        e = launch_strided_tma(a, s.gin, s.gout, &ti, &to, st);
+      if (encode_stage_map(p, s.gin, s.axis, s.tma_W, in, &ti) &&
+          encode_stage_map(p, s.gout, s.axis, s.tma_W, out, &to)) {
+        StridedArgs at = a;
+        at.W = s.tma_W;
+        at.colblocks = reinterpret_cast<const int2*>(p->d_state + s.tma_cb_off);
+        at.ncolblocks = s.tma_ncb;
+        e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
         done = true;
       }
     }
     if (!done) e = launch_strided(a, st);
+  } else if (s.kind == S_REAL) {
+    RealArgs a;
+    a.rin = reinterpret_cast<const float*>(bufs[s.src]);
+    a.cout = static_cast<float2*>(bufs[s.dst]);
+    a.cin = static_cast<const float2*>(bufs[s.src]);
+    a.rout = static_cast<float*>(bufs[s.dst]);
+    a.nlines = s.nlines;
+    a.ap = p->rplan;
+    a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[p->rplan.L]);
+    a.tw2 = reinterpret_cast<const float2*>(p->d_state + p->tw_off[2 * p->rplan.L]);
+    a.dir = s.sign;
+    a.scale = s.scaled ? (float)s.scale_value : 1.0f;
+    a.status = reinterpret_cast<int*>(p->d_state);
+    e = launch_real_spec(a, st);
   } else {
     BoxArgs a;
     a.in = in;
@@ -768,7 +842,6 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     return fail(TFFT_EINVAL, "grid_ndims must be 0..min(3, ndims - 1) (Sec. 3.6)");
   if (grid_ndims > 0 && !grid) return fail(TFFT_EINVAL, "grid is NULL");
   if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
-  if (kind == TFFT_R2C) return fail(TFFT_EUNSUPPORTED, "real-to-complex plans are not built yet");
   if (precision != TFFT_FP32) return fail(TFFT_EUNSUPPORTED, "precision must be TFFT_FP32");
   if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA)) return fail(TFFT_EINVAL, "unknown flag bits");
   auto p = new tfft_plan_s();
@@ -785,6 +858,15 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     }
     p->shape[m] = p->cshape[m] = shape[m];
     n *= shape[m];
+  }
+  p->nreal = n;
+  if (kind == TFFT_R2C) {
+    if (shape[ndims - 1] % 2) {
+      delete p;
+      return fail(TFFT_EUNSUPPORTED, "real-to-complex needs an even innermost extent");
+    }
+    p->cshape[ndims - 1] = shape[ndims - 1] / 2 + 1;  // Hermitian half (footnote to Eq. multifft)
+    n = n / shape[ndims - 1] * p->cshape[ndims - 1];
   }
   p->nelems = n;
   int64_t nr = 1;
@@ -813,9 +895,23 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     build_layout(p, p->cshape, s, p->st[s]);
     p->st[s].state_off = image_add(p, p->st[s].offset.data(), p->st[s].offset.size() * 8);
   }
+  if (kind == TFFT_R2C) build_layout(p, p->shape, 0, p->real0);
   // per-length FFT plans and twiddle table slots (a plan whose lengths do not
   // factor into 2, 3, 5 up to 4096 still redistributes, but does not transform)
+  if (kind == TFFT_R2C) {
+    const int Lh = (int)(p->shape[ndims - 1] / 2);
+    int width = 0;
+    p->rplan = AxisPlan{};
+    if (spec_plan(Lh, false, p->nelems, p->rplan, width)) {
+      p->rplan.width = width;
+      if (!p->tw_off.count(Lh)) p->tw_off[Lh] = image_add(p, nullptr, (size_t)Lh * sizeof(float2));
+      if (!p->tw_off.count(2 * Lh)) p->tw_off[2 * Lh] = image_add(p, nullptr, (size_t)2 * Lh * sizeof(float2));
+    } else {
+      p->transformable = false;  // half length without a compiled real-line kernel
+    }
+  }
   for (int m = 0; m < ndims; ++m) {
+    if (kind == TFFT_R2C && m == ndims - 1) break;  // the innermost axis is the real pass
     const int L = (int)p->cshape[m];
     if (p->aplan.count(L)) continue;
     AxisPlan ap, aps;
@@ -834,7 +930,7 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     if (spec_plan(L, true, p->nelems, aps, width)) aps.width = width;
     p->aplan[L] = ap;
     p->aplan_s[L] = aps;
-    p->tw_off[L] = image_add(p, nullptr, (size_t)L * sizeof(float2));
+    if (!p->tw_off.count(L)) p->tw_off[L] = image_add(p, nullptr, (size_t)L * sizeof(float2));
   }
   // exchange boxes between adjacent stages, both directions
   for (int s = 1; s <= p->g; ++s) {
@@ -884,7 +980,12 @@ int tfft_plan_stage_axis(tfft_plan p, int stage, int* axis) {
 int tfft_plan_stage_elems(tfft_plan p, int stage, int real, int64_t* elems) {
   if (!p || !elems) return fail(TFFT_EINVAL, "NULL argument");
   if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
-  if (real) return fail(TFFT_EINVAL, "not a real-to-complex plan");
+  if (real) {
+    if (p->kind != TFFT_R2C) return fail(TFFT_EINVAL, "not a real-to-complex plan");
+    if (stage != 0) return fail(TFFT_EINVAL, "the real buffer is the stage-0 alignment");
+    *elems = p->real0.total;
+    return TFFT_OK;
+  }
   *elems = p->st[stage].total;
   return TFFT_OK;
 }
@@ -894,8 +995,9 @@ int tfft_plan_local_box(tfft_plan p, int stage, int real, int rank, int64_t* sta
   if (!p || !start || !size || !offset) return fail(TFFT_EINVAL, "NULL argument");
   if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
   if (rank < 0 || rank >= p->nranks) return fail(TFFT_EINVAL, "rank out of range");
-  if (real) return fail(TFFT_EINVAL, "not a real-to-complex plan");
-  const LayoutH& L = p->st[stage];
+  if (real && p->kind != TFFT_R2C) return fail(TFFT_EINVAL, "not a real-to-complex plan");
+  if (real && stage != 0) return fail(TFFT_EINVAL, "the real buffer is the stage-0 alignment");
+  const LayoutH& L = real ? p->real0 : p->st[stage];
   for (int m = 0; m < p->d; ++m) {
     start[m] = L.start[(size_t)rank * p->d + m];
     size[m] = L.size[(size_t)rank * p->d + m];
@@ -932,7 +1034,7 @@ int tfft_plan_workspace_bytes(tfft_plan p, int mode, int keep_input, size_t* byt
   if (!p || !bytes) return fail(TFFT_EINVAL, "NULL argument");
   const size_t stage = (size_t)p->nelems * sizeof(float2);
   switch (mode) {
-    case TFFT_MODE_FUSED: *bytes = keep_input ? stage : 0; break;
+    case TFFT_MODE_FUSED: *bytes = (keep_input || p->kind == TFFT_R2C) ? stage : 0; break;
     case TFFT_MODE_UNFUSED:
     case TFFT_MODE_PACKED: *bytes = 2 * stage; break;
     default: return fail(TFFT_EINVAL, "unknown mode");
@@ -1003,6 +1105,15 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
   const Step& s = it->second[index];
   std::string nm;
   int64_t elems = 0;
+  if (s.kind == S_REAL) {
+    nm = std::string(sign == TFFT_FORWARD ? "fft_r2c_L" : "fft_c2r_L") + std::to_string(2 * p->rplan.L);
+    *bytes = p->nreal * (int64_t)sizeof(float) + p->nelems * (int64_t)sizeof(float2);
+    if (name_len > 0) {
+      std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
+      name[name_len - 1] = 0;
+    }
+    return TFFT_OK;
+  }
   if (s.kind == S_BOX) {
     nm = "box_copy";
     const ExchangeBoxes* X = nullptr;
@@ -1071,10 +1182,14 @@ int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, voi
   rc = check_ptr(out, "out");
   if (rc) return rc;
   const size_t stage = (size_t)p->nelems * sizeof(float2);
+  const bool r2c = p->kind == TFFT_R2C;
+  const size_t real_bytes = (size_t)p->nreal * sizeof(float);
+  const size_t in_bytes = (r2c && sign == TFFT_FORWARD) ? real_bytes : stage;
+  const size_t out_bytes = (r2c && sign == TFFT_BACKWARD) ? real_bytes : stage;
   {
     const char* a = static_cast<const char*>(in);
     const char* b = static_cast<const char*>(out);
-    if (a < b + stage && b < a + stage) return fail(TFFT_EINVAL, "in and out overlap");
+    if (a < b + out_bytes && b < a + in_bytes) return fail(TFFT_EINVAL, "in and out overlap");
   }
   std::vector<Step> steps = p->steps[{sign, mode}];
   void* w0 = nullptr;
@@ -1086,9 +1201,13 @@ int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, voi
       if (rc) return rc;
       if (work_bytes < stage) return fail(TFFT_EWORKSPACE, "fused workspace must hold one stage buffer");
       w0 = work;
+    } else if (r2c) {
+      return fail(TFFT_EWORKSPACE, "real-to-complex plans need a workspace of one complex stage buffer");
     } else {
       destroy = true;
     }
+    // a complex-to-real backward uses its input as scratch
+    if (r2c && sign == TFFT_BACKWARD) destroy = true;
   } else {
     if (!work || work_bytes < 2 * stage)
       return fail(TFFT_EWORKSPACE, "this mode needs a workspace of two stage buffers");
@@ -1100,9 +1219,11 @@ int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, voi
   if (work) {
     const char* a = static_cast<const char*>(work);
     const size_t wb = (mode == TFFT_MODE_FUSED) ? stage : 2 * stage;
-    for (const void* q : {in, static_cast<const void*>(out)}) {
-      const char* b = static_cast<const char*>(q);
-      if (a < b + stage && b < a + wb) return fail(TFFT_EINVAL, "work overlaps in or out");
+    const void* ptrs[2] = {in, out};
+    const size_t sizes[2] = {in_bytes, out_bytes};
+    for (int k = 0; k < 2; ++k) {
+      const char* b = static_cast<const char*>(ptrs[k]);
+      if (a < b + sizes[k] && b < a + wb) return fail(TFFT_EINVAL, "work overlaps in or out");
     }
   }
   assign_buffers(steps, destroy);

@@ -25,6 +25,23 @@ struct ContigArgs {
   int* status;       // device status word
 };
 
+// Real-to-complex (dir -1) or complex-to-real (dir +1) along the innermost
+// axis: lines of N = 2 L reals <-> lines of L + 1 complex (Hermitian half),
+// computed with one complex FFT of length L per line.
+struct RealArgs {
+  const float* rin;     // r2c input (nlines x 2L floats)
+  float2* cout;         // r2c output (nlines x (L + 1))
+  const float2* cin;    // c2r input
+  float* rout;          // c2r output
+  int64_t nlines;
+  AxisPlan ap;          // plan of the length-L complex FFT
+  const float2* tw;     // L roots exp(-2 pi i m / L)
+  const float2* tw2;    // 2L roots exp(-2 pi i m / 2L)
+  int dir;
+  float scale;
+  int* status;
+};
+
 // 1-D FFT along axis `axis` < d - 1 with the redistribution fused into the
 // loads (input layout lin) and the stores (output layout lout).  A tile is
 // one value of the remaining axes ("outer" index) times a block of up to W
@@ -98,11 +115,14 @@ bool kernel_supports_E(int E);
 bool spec_plan(int L, bool strided, int64_t nelems, AxisPlan& ap, int& width);
 cudaError_t launch_contig_spec(const ContigArgs& a, cudaStream_t s);
 cudaError_t launch_strided_spec(const StridedArgs& a, cudaStream_t s);
+cudaError_t launch_real_spec(const RealArgs& a, cudaStream_t s);
 
 // TMA-staged passes (tfft_tma.cu).  tmap_* point to host CUtensorMap objects.
-bool tma_width(int L, int& W);
+// tma_strided_variant: elements per thread and tile width of the strided TMA
+// variant of length L with width want_W if compiled, else the default one.
+bool tma_strided_variant(int L, int want_W, int want_E, int& E, int& W);
 bool tma_contig_plan(int L, int& E, int& B);
-cudaError_t launch_strided_tma(const StridedArgs& a, const TmaGeo& gin, const TmaGeo& gout,
+cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gin, const TmaGeo& gout,
                                const void* tmap_in, const void* tmap_out, cudaStream_t s);
 cudaError_t launch_contig_tma(const ContigArgs& a, cudaStream_t s);
 

@@ -174,8 +174,13 @@ __device__ __forceinline__ void tile_coords(const TmaGeo& G, int axis, int k, in
 
 // ------------------------------------------------------------ strided, TMA
 
+// Shared memory of the strided TMA kernel: three L x (W + 1) tile buffers.
+__host__ __device__ constexpr size_t strided_tma_smem(int L, int W) {
+  return 3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t);
+}
+
 template <int L, int E, int W, int... Rs>
-__global__ void __launch_bounds__(W * (L / E), 1)
+__global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1024 ? 2 : 1)
     k_strided_tma(const StridedArgs a, const TmaGeo gin, const TmaGeo gout,
                   const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout) {
   constexpr int T = L / E, NST = sizeof...(Rs);
@@ -367,7 +372,7 @@ __global__ void __launch_bounds__((L / E) * B, 1)
       } else {
         constexpr int Rp = radix_at<s - 1, Rs...>();
         constexpr int Nsp = Ns / Rp;
-        __syncthreads();
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
 #pragma unroll
         for (int q = 0; q < E / Rp; ++q)
 #pragma unroll
@@ -375,7 +380,7 @@ __global__ void __launch_bounds__((L / E) * B, 1)
             const int pos = stockham_out_index(jt + q * T, Nsp, Rp, r);
             sl[pos + (pos >> 3)] = v[q * Rp + r];
           }
-        __syncthreads();
+        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
 #pragma unroll
         for (int q = 0; q < E / R; ++q)
 #pragma unroll
@@ -430,7 +435,7 @@ cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo
   static cudaError_t attr = allow_smem(kern);
   if (attr != cudaSuccess) return attr;
   if (a.W != W) return cudaErrorInvalidValue;
-  const size_t smem = 3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t);
+  const size_t smem = strided_tma_smem(L, W);
   const int threads = W * (L / E);
   static const int64_t slots = persistent_grid(kern, threads, smem, int64_t(1) << 40);
   const int64_t ntiles = a.nouter * a.ncolblocks;
@@ -455,64 +460,75 @@ cudaError_t run_contig_tma(const ContigArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Lengths with a TMA variant: L, strided elements per thread and tile width,
-// contiguous elements per thread and lines per tile, radices.
-#define TFFT_TMA_SPECS(X)                 \
-  X(64, 8, 32, 8, 32, 8, 8)               \
-  X(128, 16, 32, 16, 16, 16, 8)           \
-  X(256, 16, 32, 16, 8, 16, 16)           \
-  X(512, 16, 16, 8, 4, 8, 8, 8)
+// Strided TMA variants: length, elements per thread, tile width, radices.
+// The first row of a length is its default; tma_strided_width() can pick
+// another (autotuning).
+#define TFFT_TMA_STRIDED(X)     \
+  X(64, 8, 32, 8, 8)            \
+  X(128, 16, 32, 16, 8)         \
+  X(256, 16, 32, 16, 16)        \
+  X(512, 16, 16, 8, 8, 8)       \
+  X(512, 16, 8, 8, 8, 8)        \
+  X(512, 8, 8, 8, 8, 8)
+
+// Contiguous TMA variants: length, elements per thread, lines per tile, radices.
+#define TFFT_TMA_CONTIG(X)      \
+  X(64, 8, 32, 8, 8)            \
+  X(128, 16, 16, 16, 8)         \
+  X(256, 16, 8, 16, 16)         \
+  X(512, 16, 8, 8, 8, 8)
 
 }  // namespace
 
-bool tma_width(int L, int& W) {
-  switch (L) {
-#define X(LL, ES, WW, EC, BB, ...) \
-  case LL:                         \
-    W = WW;                        \
-    return true;
-    TFFT_TMA_SPECS(X)
-#undef X
-    default:
-      return false;
+bool tma_strided_variant(int L, int want_W, int want_E, int& E, int& W) {
+  bool found = false;
+#define X(LL, EE, WW, ...)                                             \
+  if (LL == L) {                                                        \
+    const bool match = WW == want_W && (want_E == 0 || EE == want_E);  \
+    if (!found || match) {                                              \
+      E = EE;                                                           \
+      W = WW;                                                           \
+      found = true;                                                     \
+      if (match) return true;                                           \
+    }                                                                   \
   }
+  TFFT_TMA_STRIDED(X)
+#undef X
+  return found;
 }
 
 bool tma_contig_plan(int L, int& E, int& B) {
   switch (L) {
-#define X(LL, ES, WW, EC, BB, ...) \
-  case LL:                         \
-    E = EC;                        \
-    B = BB;                        \
+#define X(LL, EE, BB, ...) \
+  case LL:                 \
+    E = EE;                \
+    B = BB;                \
     return true;
-    TFFT_TMA_SPECS(X)
+    TFFT_TMA_CONTIG(X)
 #undef X
     default:
       return false;
   }
 }
 
-cudaError_t launch_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo& go, const void* tmap_in,
-                               const void* tmap_out, cudaStream_t s) {
+cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gi, const TmaGeo& go,
+                               const void* tmap_in, const void* tmap_out, cudaStream_t s) {
   const CUtensorMap& ti = *static_cast<const CUtensorMap*>(tmap_in);
   const CUtensorMap& to = *static_cast<const CUtensorMap*>(tmap_out);
-  switch (a.ap.L) {
-#define X(LL, ES, WW, EC, BB, ...) \
-  case LL:                         \
-    return run_strided_tma<LL, ES, WW, __VA_ARGS__>(a, gi, go, ti, to, s);
-    TFFT_TMA_SPECS(X)
+#define X(LL, EE, WW, ...)                   \
+  if (a.ap.L == LL && E == EE && a.W == WW) \
+    return run_strided_tma<LL, EE, WW, __VA_ARGS__>(a, gi, go, ti, to, s);
+  TFFT_TMA_STRIDED(X)
 #undef X
-    default:
-      return cudaErrorInvalidValue;
-  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_contig_tma(const ContigArgs& a, cudaStream_t s) {
   switch (a.ap.L) {
-#define X(LL, ES, WW, EC, BB, ...) \
-  case LL:                         \
-    return run_contig_tma<LL, EC, BB, __VA_ARGS__>(a, s);
-    TFFT_TMA_SPECS(X)
+#define X(LL, EE, BB, ...) \
+  case LL:                 \
+    return run_contig_tma<LL, EE, BB, __VA_ARGS__>(a, s);
+    TFFT_TMA_CONTIG(X)
 #undef X
     default:
       return cudaErrorInvalidValue;

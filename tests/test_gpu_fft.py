@@ -181,3 +181,62 @@ def test_full_size_512_pencil_sampled(cuda_device):
     back = p.inverse(y)
     diff = torch.linalg.vector_norm((back - b0).to(torch.complex128)) / torch.linalg.vector_norm(b0.to(torch.complex128))
     assert float(diff) <= RTOL_FP32
+
+
+R2C_CASES = [
+    ((32, 64, 256), (8,)),           # the r2c slab workload's innermost length, 8 ranks
+    ((16, 32, 64), (2, 2)),          # r2c on a pencil grid
+    ((12, 10, 128), (3,)),           # uneven slab
+    ((24, 64), (4,)),                # 2-D
+    ((64,), ()),                     # 1-D real line
+]
+
+
+@pytest.mark.parametrize("shape,grid", R2C_CASES)
+def test_r2c_c2r_vs_oracle(cuda_device, shape, grid):
+    """Footnote to Eq. multifft: real input, Hermitian half on the last axis;
+    fused, unfused and packed paths agree bit for bit."""
+    from paper_1804_09536_gb300.plan import Plan
+    g = len(grid)
+    x = inputs.normal_real(shape, seed=0).numpy()
+    cshape = shape[:-1] + (shape[-1] // 2 + 1,)
+    b0 = R.scatter(x, grid, 0)
+    want = dft.distributed_rfft_forward(b0.astype(np.float64), shape, grid)
+    p = Plan(shape, grid, kind="r2c", device=cuda_device)
+    outs, backs = {}, {}
+    for mode in ("fused", "unfused", "packed"):
+        xin = to_dev(b0, cuda_device)
+        y = p.forward(xin, mode=mode)
+        torch.cuda.synchronize()
+        assert np.array_equal(bits(xin), b0.view(np.uint8)), "r2c keeps its input"
+        assert rel_l2(y.cpu().numpy(), want) <= RTOL_FP32, mode
+        outs[mode] = bits(y)
+        z = p.inverse(y.clone(), mode=mode)
+        torch.cuda.synchronize()
+        back = z.cpu().numpy()
+        want_b = dft.distributed_irfft_backward(want, shape, grid)
+        assert rel_l2(back, want_b) <= RTOL_FP32, mode
+        assert rel_l2(back, b0) <= RTOL_FP32
+        backs[mode] = bits(z)
+    for m in ("unfused", "packed"):
+        assert np.array_equal(outs["fused"], outs[m])
+        assert np.array_equal(backs["fused"], backs[m])
+    # the gathered spectrum is the oracle's r2c of the global array
+    yg = p.gather(torch.from_numpy(np.frombuffer(outs["fused"].tobytes(), np.complex64).copy()), g)
+    assert rel_l2(yg.numpy(), dft.rfftn_forward(x.astype(np.float64))) <= RTOL_FP32
+
+
+def test_c2r_ignores_dc_and_nyquist_imaginary_parts(cuda_device):
+    """c2r reading: Im of k = 0 and k = N/2 on the last axis do not contribute."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (8, 16, 64), (2,)
+    p = Plan(shape, grid, kind="r2c", device=cuda_device)
+    x = inputs.normal_real(shape, seed=2).numpy()
+    y = p.forward(to_dev(R.scatter(x, grid, 0), cuda_device))
+    yg = p.gather(y, 1).cpu().numpy()
+    pert = yg.copy()
+    pert[..., 0] += 0.5j
+    pert[..., -1] -= 0.25j
+    z = p.inverse(to_dev(R.scatter(pert, grid, 1), cuda_device))
+    want = dft.irfftn_backward(pert.astype(np.complex128), shape[-1])
+    assert rel_l2(p.gather(z, 0, real=True).cpu().numpy(), want) <= RTOL_FP32
