@@ -213,6 +213,30 @@ int tfft_plan_device_status(tfft_plan plan, int *status, int reset, void *stream
  */
 int tfft_plan_set_launch_events(tfft_plan plan, void *const *events, int count);
 
+/*
+ * Fused transform whose scratch lives in a fixed device array inside this
+ * library, for callers that may not allocate device memory -- e.g. a plugin
+ * running in a host framework that owns all device memory through its own
+ * allocator, where an extra cudaMalloc is forbidden or finds no memory.  The
+ * paper has no counterpart; it is an interface convenience.
+ *
+ * Same result as tfft_execute(plan, sign, TFFT_MODE_FUSED, in, out, work, ...)
+ * with a caller-allocated workspace: the input is kept.  Nothing is
+ * allocated: the scratch is a static __device__ array of
+ * TFFT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
+ * holds until the process exits; a plan whose stage buffer is larger is
+ * rejected with TFFT_EWORKSPACE (message in tfft_last_error()).
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents (every call overwrites what it reads, so nothing has
+ * to start at zero); calls whose work overlaps on the GPU -- on different
+ * streams, or from different threads -- race on it.
+ */
+#define TFFT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int tfft_execute_noalloc(tfft_plan plan, int sign, const void *in, void *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

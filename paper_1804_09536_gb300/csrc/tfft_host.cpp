@@ -87,6 +87,8 @@ struct ExchangeBoxes {  // one adjacent-stage exchange
 
 }  // namespace
 
+void tfft::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct tfft_plan_s {
   int d = 0, g = 0, kind = TFFT_C2C, precision = TFFT_FP32, flags = 0;
   int64_t shape[MAXD] = {1, 1, 1, 1};

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "tfft_common.cuh"
 
 namespace tfft {
@@ -106,6 +108,9 @@ cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s);
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
 cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+
+// Message returned by tfft_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 // Limits of the kernels, used by the planner.
 bool kernel_supports_E(int E);
