@@ -147,7 +147,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if rank == 0 or world > 1:
         _build.build()
-    plan = Plan(SHAPE, GRID, device=dev)
+    plan = Plan(SHAPE, GRID, device=dev, tma=not args.no_tma)
     stream = torch.cuda.current_stream()
 
     # seeded input: complex N(0, 1), the same array on every replica
@@ -393,6 +393,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--shape", type=int, nargs="+", default=list(SHAPE))
     ap.add_argument("--grid", type=int, nargs="*", default=list(GRID))
+    ap.add_argument("--no-tma", action="store_true",
+                    help="plain load/store passes only (comparison and profiling)")
     ap.add_argument("--profile-only", action="store_true",
                     help="headline loop only (no comparison paths, e2e or CPU baseline)")
     args = ap.parse_args()

@@ -210,6 +210,56 @@ struct Dft<16> {
   }
 };
 
+// exp(-2 pi i m / 32) for 0 <= m < 32, from cos(pi j / 16), j = 0..8, by
+// the symmetries of the circle.
+TFFT_HD float2 w32(int m) {
+  const float c[9] = {1.0f,
+                      0.98078528040323044913f,
+                      0.92387953251128675613f,
+                      0.83146961230254523708f,
+                      0.70710678118654752440f,
+                      0.55557023301960222474f,
+                      0.38268343236508977173f,
+                      0.19509032201612826785f,
+                      0.0f};
+  // cos and sin of pi m / 16 for m in [0, 32)
+  const int q = m & 7, oct = m >> 3;  // m = 8 oct + q
+  float cs, sn;
+  switch (oct) {
+    case 0: cs = c[q]; sn = c[8 - q]; break;
+    case 1: cs = -c[8 - q]; sn = c[q]; break;
+    case 2: cs = -c[q]; sn = -c[8 - q]; break;
+    default: cs = c[8 - q]; sn = -c[q]; break;
+  }
+  return make_float2(cs, -sn);
+}
+
+template <>
+struct Dft<32> {
+  TFFT_HD static void run(float2* v) {
+    // 32 = 4 x 8: inner DFT8 over n2 for each n1 (n = 4 n2 + n1), twiddle
+    // exp(-2 pi i n1 k1 / 32), outer DFT4 over n1; output k = k1 + 8 k2.
+    float2 y[4][8];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+#pragma unroll
+      for (int n2 = 0; n2 < 8; ++n2) y[n1][n2] = v[4 * n2 + n1];
+      Dft<8>::run(y[n1]);
+    }
+#pragma unroll
+    for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+      for (int k1 = 1; k1 < 8; ++k1) y[n1][k1] = cmul(y[n1][k1], w32(n1 * k1));
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+      float2 z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+      Dft<4>::run(z);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 8 * k2] = z[k2];
+    }
+  }
+};
+
 // ------------------------------------------------------------ Stockham schedule
 //
 // A length-L FFT with radices R_0, R_1, ... (product L).  Stage s has span

@@ -68,7 +68,7 @@ __device__ __forceinline__ int opaque_tid_y() {
 // (half that for the 20-element plans, whose butterflies need more registers).
 __host__ __device__ constexpr int min_blocks(int E, int threads, int target) {
   const int t = (E >= 20 ? target / 2 : target) / threads;
-  return t > 0 ? t : 1;
+  return t > 1 ? t : (E >= 32 && threads <= 256 ? 2 : 1);
 }
 
 // Synchronises the threads of one line: a warp (or part of one) when a line
@@ -403,7 +403,7 @@ cudaError_t run_strided(const StridedArgs& a, cudaStream_t s) {
   X(128, 16, 32, 16, 32, 16, 8)             \
   X(160, 20, 32, 20, 32, 5, 4, 4, 2)        \
   X(256, 16, 16, 16, 32, 16, 16)            \
-  X(512, 16, 8, 16, 16, 8, 8, 8)
+  X(512, 32, 16, 32, 16, 32, 16)
 
 struct SpecRow {
   int L, EC, B, ES, W, nst, radix[6];

@@ -461,22 +461,21 @@ cudaError_t run_contig_tma(const ContigArgs& a, cudaStream_t s) {
 }
 
 // Strided TMA variants: length, elements per thread, tile width, radices.
-// The first row of a length is its default; tma_strided_width() can pick
+// The first row of a length is its default; tma_strided_variant() can pick
 // another (autotuning).
 #define TFFT_TMA_STRIDED(X)     \
   X(64, 8, 32, 8, 8)            \
   X(128, 16, 32, 16, 8)         \
   X(256, 16, 32, 16, 16)        \
-  X(512, 16, 16, 8, 8, 8)       \
-  X(512, 16, 8, 8, 8, 8)        \
-  X(512, 8, 8, 8, 8, 8)
+  X(512, 32, 16, 32, 16)        \
+  X(512, 16, 16, 8, 8, 8)
 
 // Contiguous TMA variants: length, elements per thread, lines per tile, radices.
 #define TFFT_TMA_CONTIG(X)      \
   X(64, 8, 32, 8, 8)            \
   X(128, 16, 16, 16, 8)         \
   X(256, 16, 8, 16, 16)         \
-  X(512, 16, 8, 8, 8, 8)
+  X(512, 32, 16, 32, 16)
 
 }  // namespace
 

@@ -31,6 +31,7 @@ static void with_radix(int R, F&& f) {
     case 5: if constexpr (E % 5 == 0) f(std::integral_constant<int, 5>{}); break;
     case 8: if constexpr (E % 8 == 0) f(std::integral_constant<int, 8>{}); break;
     case 16: if constexpr (E % 16 == 0) f(std::integral_constant<int, 16>{}); break;
+    case 32: if constexpr (E % 32 == 0) f(std::integral_constant<int, 32>{}); break;
   }
 }
 
@@ -111,6 +112,7 @@ extern "C" int emulate_fft(int L, int E, const int* radix, int nst, const float*
     case 16: return run<16>(L, radix, nst, i2, o2, sign);
     case 20: return run<20>(L, radix, nst, i2, o2, sign);
     case 24: return run<24>(L, radix, nst, i2, o2, sign);
+    case 32: return run<32>(L, radix, nst, i2, o2, sign);
   }
   return -2;
 }

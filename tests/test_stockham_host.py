@@ -51,10 +51,10 @@ def _run(lib, L, E, radices, x, sign):
 CASES = []
 for radices in [(2,), (3,), (4,), (5,), (8,), (16,), (8, 8, 8), (16, 16, 2), (8, 4, 2), (4, 4, 3, 2),
                 (5, 4, 4, 2), (16, 8), (8, 16), (3, 5), (5, 3), (2, 2, 2, 2), (16, 16, 16), (4, 3),
-                (8, 3, 4), (16, 5, 2)]:
+                (8, 3, 4), (16, 5, 2), (32,), (32, 16), (16, 32), (32, 32), (32, 2)]:
     L = int(np.prod(radices))
     lcm = int(np.lcm.reduce(radices))
-    for E in (2, 3, 4, 5, 6, 8, 10, 12, 15, 16, 20, 24):
+    for E in (2, 3, 4, 5, 6, 8, 10, 12, 15, 16, 20, 24, 32):
         if E % lcm == 0 and L % E == 0:
             CASES.append((L, E, radices))
 
