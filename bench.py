@@ -119,17 +119,25 @@ def _traffic_per_launch(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     kernel source is unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    src = os.path.join(ROOT, "paper_1804_09536_gb300", "csrc", "tfft_kernels.cu")
     try:
         with open(path) as f:
             rec = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
-        if rec.get("kernels_sha256_16") != h:
+        if rec.get("kernels_sha256_16") != kernel_source_hash():
             return None
         return rec["per_launch_bytes"].get(kernel)
     except Exception:
         return None
+
+
+def kernel_source_hash() -> str:
+    """sha256 (16 hex digits) over every CUDA source and header of the library."""
+    csrc = os.path.join(ROOT, "paper_1804_09536_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- our arm
@@ -235,6 +243,10 @@ def run_ours(args):
         barrier()
         extra[mode] = a.elapsed_time(b) / ksteps
 
+    # the r2c slab workload (256^3 real, 8-rank slab): fused vs packed, forward + inverse
+    r2c = r2c_slab(plan_cls=Plan, dev=dev, steps=max(5, min(args.steps, 50)), barrier=barrier,
+                   tma=not args.no_tma)
+
     # end to end through the public API with host buffers: pinned H2D of the
     # input, forward + inverse, D2H of the result, every step
     h_in = x.cpu().pin_memory()
@@ -302,6 +314,7 @@ def run_ours(args):
                                    "unfused": round(extra["unfused"], 4),
                                    "packed": round(extra["packed"], 4)},
         "fused_vs_packed_speedup": round(extra["packed"] / ms_step, 3),
+        "r2c_slab_256": r2c,
         "e2e": {"value": round(world * FLOP_PER_STEP / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
                 "ms_per_step": round(e2e_ms, 4),
                 "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
@@ -318,6 +331,48 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def r2c_slab(plan_cls, dev, steps, barrier, tma=True):
+    """256^3 real-to-complex (output 256 x 256 x 129) on a virtual 8-rank slab,
+    forward + inverse, fused and packed; ms per step and the HBM fraction of
+    the fused path's algorithmic bytes."""
+    import torch
+    from paper_1804_09536_gb300 import inputs
+    shape, grid = (256, 256, 256), (8,)
+    p = plan_cls(shape, grid, kind="r2c", device=dev, tma=tma)
+    x = p.scatter(inputs.normal_real(shape, seed=0).to(dev), 0, real=True)
+    y = p.empty_stage(1)
+    z = p.empty_stage(0, real=True)
+    out = {}
+    nbytes = 0
+    for mode in ("fused", "packed"):
+        w = p.workspace(mode)
+
+        def one():
+            p.execute(-1, x, y, mode, w)
+            p.execute(+1, y, z, mode, w)
+        for _ in range(3):
+            one()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            one()
+        b.record()
+        barrier()
+        out[mode] = a.elapsed_time(b) / steps
+        if mode == "fused":
+            nbytes = sum(n for _, n in p.launch_info(-1, mode) + p.launch_info(+1, mode))
+    peak, _ = _peaks()
+    n = math.prod(shape)
+    return {"workload": "256x256x256 r2c float32 -> 256x256x129 complex64, virtual slab 8, forward+inverse",
+            "fused_ms": round(out["fused"], 4), "packed_ms": round(out["packed"], 4),
+            "fused_vs_packed_speedup": round(out["packed"] / out["fused"], 3),
+            "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
+            "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
+            "note": "c2r overwrites its input; the forward output is reused as the inverse's input"}
 
 
 # ---------------------------------------------------------------- oracle arm
