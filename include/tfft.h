@@ -184,6 +184,37 @@ int tfft_partial(tfft_plan plan, int stage, int axis, int sign, void *inout, voi
 int tfft_execute(tfft_plan plan, int sign, int mode, const void *in, void *out, void *work,
                  size_t work_bytes, void *stream);
 
+/*
+ * Adjoint F^H of the forward transform F of this plan (complex-to-complex
+ * plans): stage g -> stage 0.  With the paper's normalisation (1/N on the
+ * forward, Eq. multifft) F^H = (1/N) x backward (Eq. 2 is unscaled), so this
+ * runs the backward passes -- the forward's passes in reverse order, each
+ * redistribution reversed (a permutation, whose adjoint is its inverse) --
+ * with 1/N applied in the last pass (no factor under TFFT_NORM_BACKWARD).
+ * Arguments as tfft_execute().
+ */
+int tfft_adjoint(tfft_plan plan, int mode, const void *in, void *out, void *work, size_t work_bytes,
+                 void *stream);
+
+/*
+ * Spectral-weight loss sum_k |y_k w_k|^2 over a whole stage buffer: y is
+ * complex64, w is float32 in the same layout (w[i] weighs y[i]); the sum is
+ * formed in double precision in a fixed order (deterministic) and written to
+ * d_loss[0] (device memory).  Uses scratch inside the plan state: calls on one
+ * plan must not overlap on the GPU.
+ */
+int tfft_weighted_energy(tfft_plan plan, int stage, const void *y, const float *w, double *d_loss,
+                         void *stream);
+
+/*
+ * Gradient seed of that loss: z = c * w^2 * y elementwise, c = scale * d_coef[0]
+ * (read on the device; d_coef may be NULL for c = scale).  With c = 2 g, the
+ * gradient of g * loss(F x) with respect to x is tfft_adjoint(z)
+ * (d/dRe x + i d/dIm x convention).  z may alias y.
+ */
+int tfft_weight_scale(tfft_plan plan, int stage, const void *y, const float *w, const double *d_coef,
+                      double scale, void *z, void *stream);
+
 /* Number of kernel launches tfft_execute() makes in a mode and direction. */
 int tfft_plan_num_launches(tfft_plan plan, int sign, int mode, int *nlaunches);
 

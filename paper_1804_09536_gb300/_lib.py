@@ -53,6 +53,9 @@ SIGNATURES = {
     "tfft_execute": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp],
     "tfft_plan_num_launches": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "tfft_plan_set_launch_events": [_vp, ctypes.POINTER(_vp), ctypes.c_int],
+    "tfft_adjoint": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp],
+    "tfft_weighted_energy": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "tfft_weight_scale": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp],
     "tfft_execute_noalloc": [_vp, ctypes.c_int, _vp, _vp, _vp],
     "tfft_plan_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],
     "tfft_plan_launch_info": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtfft.so")
 
-SOURCES = ["tfft_kernels.cu", "tfft_spec.cu", "tfft_tma.cu", "tfft_noalloc.cu", "tfft_host.cpp"]
+SOURCES = ["tfft_kernels.cu", "tfft_spec.cu", "tfft_tma.cu", "tfft_noalloc.cu", "tfft_pointwise.cu", "tfft_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,7 +46,7 @@ def _stale(target: str, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh", ".map"))]
     headers.append(os.path.join(INCLUDE, "tfft.h"))
     procs, objs = [], []
     for src in SOURCES:
@@ -72,7 +72,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
         msg = "\n".join(f"--- {s} ---\n{t}" for s, t in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     if force or _stale(LIB, objs):
-        cmd = [nvcc(), "-shared", "-o", LIB + ".tmp"] + objs + ARCH + ["-cudart", "static"]
+        cmd = [nvcc(), "-shared", "-o", LIB + ".tmp"] + objs + ARCH + [
+            "-cudart", "static", "-Xlinker", "--version-script=" + os.path.join(CSRC, "exports.map")]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)

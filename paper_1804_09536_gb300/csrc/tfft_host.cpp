@@ -52,6 +52,7 @@ struct LayoutH {
 };
 
 enum StepKind { S_CONTIG, S_STRIDED, S_BOX, S_REAL };
+constexpr int kAdjoint = 2;  // key of the adjoint's step list
 enum BufId { BUF_IN, BUF_OUT, BUF_W0, BUF_W1 };
 
 struct Step {
@@ -102,6 +103,7 @@ struct tfft_plan_s {
   AxisPlan rplan{};    // complex FFT of half the innermost length (R2C)
   bool transformable = true;  // every axis length has an FFT plan
   bool use_tma = true;        // TMA-staged passes where their conditions hold
+  size_t red_off = 0;         // reduction scratch in the state (kReductionParts doubles)
   std::vector<LayoutH> st;
   std::map<int, AxisPlan> aplan;   // contiguous-line passes
   std::map<int, AxisPlan> aplan_s; // strided passes
@@ -892,6 +894,7 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
   // stage layouts and their rank offset tables
   p->use_tma = !(flags & TFFT_NO_TMA);
   image_add(p, nullptr, 256);  // device status word(s) at offset 0
+  p->red_off = image_add(p, nullptr, kReductionParts * sizeof(double));
   p->st.resize(p->g + 1);
   for (int s = 0; s <= p->g; ++s) {
     build_layout(p, p->cshape, s, p->st[s]);
@@ -944,6 +947,20 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     for (int sign : {TFFT_FORWARD, TFFT_BACKWARD})
       for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED})
         p->steps[{sign, mode}] = build_steps(p, sign, mode);
+    // the adjoint of the forward (kAdjoint): the backward steps, with 1/N on
+    // the last pass when the forward carries the normalisation
+    if (p->kind == TFFT_C2C)
+      for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED}) {
+        std::vector<Step> v = build_steps(p, TFFT_BACKWARD, mode);
+        if (!(p->flags & TFFT_NORM_BACKWARD))
+          for (int k = (int)v.size() - 1; k >= 0; --k)
+            if (v[k].kind != S_BOX) {
+              v[k].scaled = true;
+              v[k].scale_value = 1.0 / (double)p->nelems;
+              break;
+            }
+        p->steps[{kAdjoint, mode}] = v;
+      }
     // column blocks for in-place partial transforms of every stage
     for (int s = 0; s <= p->g; ++s)
       for (auto& kv : p->aplan_s) get_colblocks(p, s, s, strided_width(kv.second));
@@ -1172,8 +1189,53 @@ int tfft_plan_set_launch_events(tfft_plan p, void* const* events, int count) {
   return TFFT_OK;
 }
 
+static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
+                        size_t work_bytes, void* stream);
+
 int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, void* work,
                  size_t work_bytes, void* stream) {
+  return execute_impl(p, sign, sign, mode, in, out, work, work_bytes, stream);
+}
+
+int tfft_adjoint(tfft_plan p, int mode, const void* in, void* out, void* work, size_t work_bytes,
+                 void* stream) {
+  if (p && p->kind != TFFT_C2C) return fail(TFFT_EUNSUPPORTED, "the adjoint is built for complex-to-complex plans");
+  return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, in, out, work, work_bytes, stream);
+}
+
+int tfft_weighted_energy(tfft_plan p, int stage, const void* y, const float* w, double* d_loss, void* stream) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+  int rc = check_ptr(y, "y");
+  if (rc) return rc;
+  if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
+  if (!d_loss || (reinterpret_cast<uintptr_t>(d_loss) & 7)) return fail(TFFT_EINVAL, "d_loss is NULL or misaligned");
+  cudaError_t e = launch_weighted_energy(static_cast<const float2*>(y), w, p->st[stage].total,
+                                         reinterpret_cast<double*>(p->d_state + p->red_off), kReductionParts,
+                                         d_loss, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return TFFT_OK;
+}
+
+int tfft_weight_scale(tfft_plan p, int stage, const void* y, const float* w, const double* d_coef, double scale,
+                      void* z, void* stream) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+  int rc = check_ptr(y, "y");
+  if (rc) return rc;
+  rc = check_ptr(z, "z");
+  if (rc) return rc;
+  if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
+  cudaError_t e = launch_weight_scale(static_cast<const float2*>(y), w, d_coef, scale, p->st[stage].total,
+                                      static_cast<float2*>(z), static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return TFFT_OK;
+}
+
+static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
+                        size_t work_bytes, void* stream) {
   if (!p) return fail(TFFT_EINVAL, "plan is NULL");
   if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
   if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
@@ -1193,7 +1255,7 @@ int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, voi
     const char* b = static_cast<const char*>(out);
     if (a < b + out_bytes && b < a + in_bytes) return fail(TFFT_EINVAL, "in and out overlap");
   }
-  std::vector<Step> steps = p->steps[{sign, mode}];
+  std::vector<Step> steps = p->steps[{key, mode}];
   void* w0 = nullptr;
   void* w1 = nullptr;
   bool destroy = false;

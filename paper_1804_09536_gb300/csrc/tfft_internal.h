@@ -109,6 +109,14 @@ cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
 cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
 
+// Spectral-weight loss pieces (tfft_pointwise.cu).  The reduction uses
+// `nparts` doubles of plan-state scratch.
+constexpr int kReductionParts = 1024;
+cudaError_t launch_weighted_energy(const float2* y, const float* w, int64_t n, double* parts, int nparts,
+                                   double* out, cudaStream_t s);
+cudaError_t launch_weight_scale(const float2* y, const float* w, const double* coef, double scale, int64_t n,
+                                float2* z, cudaStream_t s);
+
 // Message returned by tfft_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 

@@ -1,0 +1,88 @@
+"""GPU: adjoint transform, spectral-weight loss and its autograd gradient (needs a GPU).
+
+Pinned against the oracle's loss / gradient (itself pinned to FP64 central
+differences and the adjoint identity in tests/test_oracle_loss.py) and against
+FP64 central differences of the oracle loss directly, on 32^3.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dft, loss as oloss, redistribute as R
+from paper_1804_09536_gb300 import inputs
+from gpu_util import RTOL_FP32, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((64, 32, 16), (4, 8)),
+                                        ((16, 24, 20), (2, 3))])
+def test_adjoint_identity_and_oracle(cuda_device, shape, grid):
+    from paper_1804_09536_gb300.plan import Plan
+    p = Plan(shape, grid, device=cuda_device)
+    g = len(grid)
+    x = inputs.normal_complex(shape, seed=1).numpy()
+    y = inputs.normal_complex(shape, seed=2).numpy()
+    fx = p.forward(to_dev(R.scatter(x, grid, 0), cuda_device)).cpu().numpy()
+    fhy = p.adjoint(to_dev(R.scatter(y, grid, g), cuda_device)).cpu().numpy()
+    lhs = np.vdot(fx.astype(np.complex128), R.scatter(y, grid, g).astype(np.complex128))
+    rhs = np.vdot(R.scatter(x, grid, 0).astype(np.complex128), fhy.astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    want = R.scatter(oloss.adjoint(y.astype(np.complex128)), grid, 0)
+    assert rel_l2(fhy, want) <= RTOL_FP32
+
+
+@pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((32, 32, 32), (4, 8))])
+def test_loss_and_gradient(cuda_device, shape, grid):
+    """The 32^3 instance of the 512^3 spectral-weight loss: value, gradient vs the oracle,
+    and directional derivatives vs FP64 central differences (h = 1e-6)."""
+    from paper_1804_09536_gb300.autograd import spectral_weight_loss
+    from paper_1804_09536_gb300.plan import Plan
+    g = len(grid)
+    p = Plan(shape, grid, device=cuda_device)
+    x = inputs.normal_complex(shape, seed=0).numpy()
+    w = inputs.uniform01_real(shape, seed=1).numpy()
+    xd = to_dev(R.scatter(x, grid, 0), cuda_device).requires_grad_(True)
+    wd = to_dev(R.scatter(w, grid, g), cuda_device)
+    L = spectral_weight_loss(xd, wd, p)
+    L.backward()
+    x64, w64 = x.astype(np.complex128), w.astype(np.float64)
+    want_L = oloss.loss(x64, w64)
+    assert abs(float(L.detach()) - want_L) <= 1e-5 * want_L
+    gx = xd.grad.detach().cpu().numpy()
+    want_g = R.scatter(oloss.grad(x64, w64), grid, 0)
+    assert rel_l2(gx, want_g) <= RTOL_FP32
+    gglob = R.gather(gx.astype(np.complex128), shape, grid, 0)
+    rng = np.random.default_rng(5)
+    for k in range(4):
+        d = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        fd = oloss.central_difference(x64, w64, d, h=1e-6)
+        an = float(np.sum(gglob.real * d.real + gglob.imag * d.imag))
+        assert abs(fd - an) <= 1e-4 * max(1.0, abs(fd)), (k, fd, an)
+
+
+def test_loss_gradient_scales_with_upstream(cuda_device):
+    """backward with an upstream gradient g: d(g * loss)/dx = g * d loss/dx (seed read on device)."""
+    from paper_1804_09536_gb300.autograd import spectral_weight_loss
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (16, 16, 16), (2, 2)
+    p = Plan(shape, grid, device=cuda_device)
+    x = to_dev(R.scatter(inputs.normal_complex(shape, seed=3).numpy(), grid, 0), cuda_device)
+    w = to_dev(R.scatter(inputs.uniform01_real(shape, seed=4).numpy(), grid, 2), cuda_device)
+    a = x.clone().requires_grad_(True)
+    spectral_weight_loss(a, w, p).backward()
+    b = x.clone().requires_grad_(True)
+    (3.5 * spectral_weight_loss(b, w, p)).backward()
+    assert rel_l2(b.grad.cpu().numpy(), 3.5 * a.grad.cpu().numpy()) <= 1e-6
+
+
+def test_weighted_energy_is_deterministic(cuda_device):
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (64, 64, 64), (2, 2)
+    p = Plan(shape, grid, device=cuda_device)
+    y = to_dev(inputs.normal_complex(shape, seed=6).numpy().reshape(-1), cuda_device)
+    w = to_dev(inputs.uniform01_real(shape, seed=7).numpy().reshape(-1), cuda_device)
+    vals = [float(p.weighted_energy(2, y, w)) for _ in range(3)]
+    assert vals[0] == vals[1] == vals[2]
+    ref = float(np.sum(np.abs(y.cpu().numpy().astype(np.complex128)) ** 2 * w.cpu().numpy().astype(np.float64) ** 2))
+    assert abs(vals[0] - ref) <= 1e-12 * ref
