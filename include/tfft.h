@@ -236,6 +236,13 @@ int tfft_plan_launch_info(tfft_plan plan, int sign, int mode, int index, char *n
 int tfft_plan_device_status(tfft_plan plan, int *status, int reset, void *stream);
 
 /*
+ * Polls a TMA pass makes on one of its copy barriers before it gives up
+ * (status bit 1, the CTA stops); 0 restores the default (2^22).  A tiny value
+ * makes the waits expire on purpose, to test the error path from the host.
+ */
+int tfft_plan_set_wait_limit(tfft_plan plan, uint32_t polls);
+
+/*
  * Timing hook: record caller-created CUDA events (cudaEvent_t as void*) on
  * the execution stream around every launch of the following tfft_execute()
  * calls: events[k] before launch k and events[n] after the last, n =
@@ -243,6 +250,50 @@ int tfft_plan_device_status(tfft_plan plan, int *status, int reset, void *stream
  * hook.  The events stay owned by the caller.
  */
 int tfft_plan_set_launch_events(tfft_plan plan, void *const *events, int count);
+
+/*
+ * Batched persistent executor: the fused transforms (one direction) of many
+ * independent complex-to-complex plans -- each with its own shape and
+ * virtual grid -- run by ONE kernel launch.  The launch's CTAs take the tiles
+ * of every pass of every transform from a shared queue in pass order; a tile
+ * of pass k of a transform waits (bounded, ~2 s, then the device status word
+ * gets TFFT_DEVICE_ETIMEOUT = 1 and the launch stops) until every tile of pass
+ * k-1 of the same transform is done.
+ *
+ *   tfft_batch_create   plans (host objects, bound before tfft_batch_bind)
+ *   tfft_batch_state_bytes / tfft_batch_bind
+ *                       caller-allocated device state; the in / out / work
+ *                       pointers of every transform are fixed at bind time
+ *                       (work[t] may be NULL: input t is then scratch)
+ *   tfft_batch_execute  one memset of the queue counters + one kernel launch,
+ *                       stream-ordered, no allocation and no host sync (so a
+ *                       CUDA graph can capture it)
+ *   tfft_batch_autotune picks, per pass kind and length, the fastest of the
+ *                       compiled tile variants (elements per thread, tile
+ *                       width / lines per group) by timing the whole batch
+ *                       (`reps` runs per candidate); it runs the batch on the
+ *                       bound buffers (their contents are overwritten) and
+ *                       synchronises.  With TFFT_AUTOTUNE_CACHE set, choices
+ *                       are read from / written to that file.
+ * The paper has no batched executor; each transform follows its plan's steps.
+ */
+typedef struct tfft_batch_s *tfft_batch;
+int tfft_batch_create(tfft_batch *batch, int count, const tfft_plan *plans, int sign);
+int tfft_batch_destroy(tfft_batch batch);
+int tfft_batch_state_bytes(tfft_batch batch, size_t *bytes);
+int tfft_batch_bind(tfft_batch batch, void *d_state, size_t bytes, const void *const *ins,
+                    void *const *outs, void *const *works, void *stream);
+int tfft_batch_execute(tfft_batch batch, void *stream);
+int tfft_batch_autotune(tfft_batch batch, int reps, void *stream);
+/* Work items (tiles) and segments (transform passes) of one execute. */
+int tfft_batch_num_items(tfft_batch batch, int64_t *items, int *segments);
+/* Executor tile variant chosen for passes of `kind` (0 contiguous, 1 strided) and length L. */
+int tfft_batch_variant(tfft_batch batch, int kind, int L, int *variant);
+/* Clock cycles a batch tile may wait for the previous pass (0: default ~2 s);
+   a tiny value makes the waits expire on purpose (error-path tests). */
+int tfft_batch_set_wait_limit(tfft_batch batch, long long cycles);
+/* Status word of the batch state (as tfft_plan_device_status). */
+int tfft_batch_device_status(tfft_batch batch, int *status, int reset, void *stream);
 
 /*
  * Fused transform whose scratch lives in a fixed device array inside this

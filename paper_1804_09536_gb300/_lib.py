@@ -56,6 +56,18 @@ SIGNATURES = {
     "tfft_adjoint": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp],
     "tfft_weighted_energy": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp],
     "tfft_weight_scale": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp],
+    "tfft_batch_create": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int],
+    "tfft_batch_destroy": [_vp],
+    "tfft_batch_state_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "tfft_batch_bind": [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                        ctypes.POINTER(_vp), _vp],
+    "tfft_batch_execute": [_vp, _vp],
+    "tfft_batch_autotune": [_vp, ctypes.c_int, _vp],
+    "tfft_batch_num_items": [_vp, _i64p, ctypes.POINTER(ctypes.c_int)],
+    "tfft_batch_variant": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "tfft_batch_set_wait_limit": [_vp, ctypes.c_longlong],
+    "tfft_plan_set_wait_limit": [_vp, ctypes.c_uint32],
+    "tfft_batch_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],
     "tfft_execute_noalloc": [_vp, ctypes.c_int, _vp, _vp, _vp],
     "tfft_plan_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],
     "tfft_plan_launch_info": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,

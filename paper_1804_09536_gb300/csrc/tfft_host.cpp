@@ -104,6 +104,7 @@ struct tfft_plan_s {
   bool transformable = true;  // every axis length has an FFT plan
   bool use_tma = true;        // TMA-staged passes where their conditions hold
   size_t red_off = 0;         // reduction scratch in the state (kReductionParts doubles)
+  uint32_t wait_limit = 1u << 22;  // polls of a bounded copy wait
   std::vector<LayoutH> st;
   std::map<int, AxisPlan> aplan;   // contiguous-line passes
   std::map<int, AxisPlan> aplan_s; // strided passes
@@ -304,6 +305,31 @@ std::pair<size_t, int64_t> get_colblocks(tfft_plan p, int lin, int lout, int W) 
   auto v = std::make_pair(off, (int64_t)blocks.size());
   p->colblocks[key] = v;
   return v;
+}
+
+// Column blocks of a (lin, lout, W) strided pass as a list (for the batch).
+std::vector<int2> colblock_list(tfft_plan p, int lin, int lout, int W) {
+  const int last = p->d - 1;
+  const int64_t N = p->cshape[last];
+  std::vector<int64_t> cuts = {0, N};
+  for (int li : {lin, lout}) {
+    const LayoutH& L = p->st[li];
+    if (L.owner[last] >= 0) {
+      const int M = p->grid[L.owner[last]];
+      for (int q = 0; q < M; ++q) {
+        int64_t n, s;
+        decompose(N, M, q, n, s);
+        cuts.push_back(s);
+      }
+    }
+  }
+  std::sort(cuts.begin(), cuts.end());
+  cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+  std::vector<int2> blocks;
+  for (size_t k = 0; k + 1 < cuts.size(); ++k)
+    for (int64_t c = cuts[k]; c < cuts[k + 1]; c += W)
+      blocks.push_back(make_int2((int)c, (int)std::min<int64_t>(W, cuts[k + 1] - c)));
+  return blocks;
 }
 
 BoxDesc make_box(int d, const int64_t* ext, int64_t src, const int64_t* ss, int64_t dst,
@@ -710,6 +736,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
     a.status = reinterpret_cast<int*>(p->d_state);
+    a.wait_limit = p->wait_limit;
     if (a.ap.tma && p->use_tma)
       e = launch_contig_tma(a, st);
     else
@@ -741,6 +768,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
     a.status = reinterpret_cast<int*>(p->d_state);
+    a.wait_limit = p->wait_limit;
     bool done = false;
     if (s.tma) {
       alignas(64) CUtensorMap ti, to;
@@ -1161,6 +1189,12 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
   return TFFT_OK;
 }
 
+int tfft_plan_set_wait_limit(tfft_plan p, uint32_t polls) {
+  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+  p->wait_limit = polls > 0 ? polls : (1u << 22);
+  return TFFT_OK;
+}
+
 int tfft_plan_device_status(tfft_plan p, int* status, int reset, void* stream) {
   if (!p || !status) return fail(TFFT_EINVAL, "NULL argument");
   if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
@@ -1295,6 +1329,363 @@ static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in
     return fail(TFFT_EINVAL, "fewer launch events than launches + 1");
   void* bufs[4] = {const_cast<void*>(in), out, w0, w1};
   return run_steps(p, steps, bufs, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+// ============================================================== batch
+
+namespace {
+
+struct BatchSegH {
+  int t, pass, kind, L, prev;
+  int64_t ntiles;
+  size_t cb_cap;  // column-block slots reserved (strided)
+};
+
+}  // namespace
+
+struct tfft_batch_s {
+  int sign = TFFT_FORWARD;
+  std::vector<tfft_plan> plans;
+  std::vector<std::vector<Step>> steps;       // per transform, fused, buffers assigned at bind
+  std::vector<BatchSegH> segs;                // pass-major
+  std::map<std::pair<int, int>, int> choice;  // (kind, L) -> executor variant
+  std::vector<void*> ins, outs, works;
+  char* d_state = nullptr;
+  size_t state_bytes = 0, ctr_off = 0, seg_off = 0, cb_off = 0;
+  int64_t nitems = 0;
+  long long spin_limit = 4000000000LL;  // clock cycles (~2 s at 2 GHz)
+};
+
+namespace {
+
+std::vector<int> batch_candidates(int kind, int L) {
+  std::vector<int> v;
+  for (int id = 0; id < batch_num_variants(); ++id) {
+    int k, l, e, bw;
+    AxisPlan ap;
+    if (batch_variant(id, k, l, e, bw, ap) && k == kind && l == L) v.push_back(id);
+  }
+  return v;
+}
+
+int64_t batch_ntiles(tfft_plan p, const Step& s, int variant) {
+  int k, l, e, bw;
+  AxisPlan ap;
+  batch_variant(variant, k, l, e, bw, ap);
+  if (s.kind == S_CONTIG) return (s.nlines + bw - 1) / bw;
+  int64_t nouter = 1;
+  for (int m = 0; m < p->d - 1; ++m)
+    if (m != s.axis) nouter *= p->cshape[m];
+  return nouter * (int64_t)colblock_list(p, s.lin, s.lout, bw).size();
+}
+
+// Items, segment table and column blocks for the current variant choices,
+// written into the bound state buffer.
+int batch_upload(tfft_batch b, cudaStream_t st) {
+  const int nseg = (int)b->segs.size();
+  std::vector<uint8_t> img(b->state_bytes, 0);
+  std::vector<BatchSeg> dsegs(nseg);
+  size_t cb = b->cb_off;
+  int64_t first = 0;
+  for (int i = 0; i < nseg; ++i) {
+    BatchSegH& h = b->segs[i];
+    tfft_plan p = b->plans[h.t];
+    const Step& s = b->steps[h.t][h.pass];
+    const int v = b->choice[{h.kind, h.L}];
+    int k, l, e, bw;
+    AxisPlan ap;
+    batch_variant(v, k, l, e, bw, ap);
+    void* bufs[4] = {b->ins[h.t], b->outs[h.t], b->works[h.t], nullptr};
+    BatchSeg& D = dsegs[i];
+    std::memset(&D, 0, sizeof(D));
+    D.kind = h.kind;
+    D.variant = v;
+    D.prev = h.prev;
+    D.transform = h.t;
+    D.first = first;
+    const float scale = s.scaled ? (float)s.scale_value : 1.0f;
+    int* status = reinterpret_cast<int*>(b->d_state);
+    if (s.kind == S_CONTIG) {
+      ContigArgs& a = D.ca;
+      a.in = static_cast<const float2*>(bufs[s.src]);
+      a.out = static_cast<float2*>(bufs[s.dst]);
+      a.nlines = s.nlines;
+      a.ap = ap;
+      a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
+      a.lines_per_cta = bw;
+      a.sign = s.sign;
+      a.scale = scale;
+      a.status = status;
+      D.ntiles = (s.nlines + bw - 1) / bw;
+    } else {
+      StridedArgs& a = D.sa;
+      a.in = static_cast<const float2*>(bufs[s.src]);
+      a.out = static_cast<float2*>(bufs[s.dst]);
+      a.lin = dev_layout(p, p->st[s.lin]);
+      a.lout = dev_layout(p, p->st[s.lout]);
+      a.d = p->d;
+      a.axis = s.axis;
+      a.ap = ap;
+      a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
+      std::vector<int2> blocks = colblock_list(p, s.lin, s.lout, bw);
+      if (blocks.size() > h.cb_cap) return fail(TFFT_EINVAL, "batch: column-block capacity exceeded");
+      std::memcpy(img.data() + cb, blocks.data(), blocks.size() * sizeof(int2));
+      a.colblocks = reinterpret_cast<const int2*>(b->d_state + cb);
+      a.ncolblocks = (int64_t)blocks.size();
+      cb += align_up(h.cb_cap * sizeof(int2), 256);
+      int oax[2] = {-1, -1}, no = 0;
+      int64_t nouter = 1;
+      for (int m = 0; m < p->d - 1; ++m)
+        if (m != s.axis) {
+          oax[no++] = m;
+          nouter *= p->cshape[m];
+        }
+      a.nouter = nouter;
+      a.oax0 = oax[0];
+      a.oax1 = oax[1];
+      a.on1 = oax[1] >= 0 ? p->cshape[oax[1]] : 1;
+      a.W = bw;
+      a.sign = s.sign;
+      a.scale = scale;
+      a.status = status;
+      D.ntiles = nouter * a.ncolblocks;
+    }
+    h.ntiles = D.ntiles;
+    first += D.ntiles;
+  }
+  b->nitems = first;
+  std::memcpy(img.data() + b->seg_off, dsegs.data(), dsegs.size() * sizeof(BatchSeg));
+  cudaError_t e = cudaMemcpyAsync(b->d_state, img.data(), img.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch state upload");
+  return TFFT_OK;
+}
+
+int batch_launch(tfft_batch b, cudaStream_t st) {
+  const size_t ctr_bytes = align_up(16 + b->segs.size() * sizeof(int), 256);
+  cudaError_t e = cudaMemsetAsync(b->d_state + b->ctr_off, 0, ctr_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (batch counters)");
+  BatchArgs a;
+  a.segs = reinterpret_cast<const BatchSeg*>(b->d_state + b->seg_off);
+  a.nsegs = (int)b->segs.size();
+  a.nitems = b->nitems;
+  a.head = reinterpret_cast<unsigned long long*>(b->d_state + b->ctr_off);
+  a.abort = reinterpret_cast<int*>(b->d_state + b->ctr_off + 8);
+  a.done = reinterpret_cast<int*>(b->d_state + b->ctr_off + 16);
+  a.status = reinterpret_cast<int*>(b->d_state);
+  a.spin_limit = b->spin_limit;
+  int grid = batch_grid();
+  if (grid > b->nitems) grid = (int)std::max<int64_t>(1, b->nitems);
+  e = launch_batch(a, grid, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return TFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int sign) {
+  if (!out) return fail(TFFT_EINVAL, "batch is NULL");
+  *out = nullptr;
+  if (count < 1 || !plans) return fail(TFFT_EINVAL, "need at least one plan");
+  if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
+  auto b = new tfft_batch_s();
+  b->sign = sign;
+  int maxpass = 0;
+  for (int t = 0; t < count; ++t) {
+    tfft_plan p = plans[t];
+    if (!p || !p->transformable || p->kind != TFFT_C2C || p->nelems >= (int64_t(1) << 31)) {
+      delete b;
+      return fail(TFFT_EUNSUPPORTED, "batch plans must be complex-to-complex, transformable, < 2^31 elements");
+    }
+    b->plans.push_back(p);
+    b->steps.push_back(p->steps[{sign, TFFT_MODE_FUSED}]);
+    for (const Step& s : b->steps.back()) {
+      const int kind = s.kind == S_CONTIG ? 0 : 1;
+      if ((s.kind != S_CONTIG && s.kind != S_STRIDED) || batch_candidates(kind, s.L).empty()) {
+        delete b;
+        return fail(TFFT_EUNSUPPORTED, "batch: no executor tile for a pass of length " + std::to_string(s.L));
+      }
+      if (!b->choice.count({kind, s.L})) b->choice[{kind, s.L}] = batch_candidates(kind, s.L)[0];
+    }
+    maxpass = std::max(maxpass, (int)b->steps.back().size());
+  }
+  // segments, pass-major; column-block capacity for the narrowest candidate
+  std::vector<std::vector<int>> idx(count);
+  size_t cb_total = 0;
+  for (int pass = 0; pass < maxpass; ++pass)
+    for (int t = 0; t < count; ++t) {
+      if (pass >= (int)b->steps[t].size()) continue;
+      const Step& s = b->steps[t][pass];
+      BatchSegH h;
+      h.t = t;
+      h.pass = pass;
+      h.kind = s.kind == S_CONTIG ? 0 : 1;
+      h.L = s.L;
+      h.prev = pass > 0 ? idx[t][pass - 1] : -1;
+      h.ntiles = 0;
+      h.cb_cap = 0;
+      if (h.kind == 1)
+        for (int v : batch_candidates(1, s.L)) {
+          int k, l, e, bw;
+          AxisPlan ap;
+          batch_variant(v, k, l, e, bw, ap);
+          h.cb_cap = std::max(h.cb_cap, colblock_list(b->plans[t], s.lin, s.lout, bw).size());
+        }
+      cb_total += align_up(h.cb_cap * sizeof(int2), 256);
+      idx[t].push_back((int)b->segs.size());
+      b->segs.push_back(h);
+    }
+  b->ctr_off = 256;
+  b->seg_off = b->ctr_off + align_up(16 + b->segs.size() * sizeof(int), 256);
+  b->cb_off = b->seg_off + align_up(b->segs.size() * sizeof(BatchSeg), 256);
+  b->state_bytes = b->cb_off + cb_total;
+  b->ins.assign(count, nullptr);
+  b->outs.assign(count, nullptr);
+  b->works.assign(count, nullptr);
+  *out = b;
+  return TFFT_OK;
+}
+
+int tfft_batch_destroy(tfft_batch b) {
+  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+  delete b;
+  return TFFT_OK;
+}
+
+int tfft_batch_state_bytes(tfft_batch b, size_t* bytes) {
+  if (!b || !bytes) return fail(TFFT_EINVAL, "NULL argument");
+  *bytes = b->state_bytes;
+  return TFFT_OK;
+}
+
+int tfft_batch_bind(tfft_batch b, void* d_state, size_t bytes, const void* const* ins, void* const* outs,
+                    void* const* works, void* stream) {
+  if (!b || !ins || !outs) return fail(TFFT_EINVAL, "NULL argument");
+  int rc = check_ptr(d_state, "d_state");
+  if (rc) return rc;
+  if (bytes < b->state_bytes) return fail(TFFT_EINVAL, "batch state buffer too small");
+  const int n = (int)b->plans.size();
+  for (int t = 0; t < n; ++t) {
+    tfft_plan p = b->plans[t];
+    if (!p->d_state) return fail(TFFT_ESTATE, "every plan of the batch must be bound first");
+    if ((rc = check_ptr(ins[t], "in"))) return rc;
+    if ((rc = check_ptr(outs[t], "out"))) return rc;
+    b->ins[t] = const_cast<void*>(ins[t]);
+    b->outs[t] = outs[t];
+    b->works[t] = works ? works[t] : nullptr;
+    if (b->works[t] && (rc = check_ptr(b->works[t], "work"))) return rc;
+    b->steps[t] = p->steps[{b->sign, TFFT_MODE_FUSED}];
+    assign_buffers(b->steps[t], b->works[t] == nullptr);
+  }
+  b->d_state = static_cast<char*>(d_state);
+  return batch_upload(b, static_cast<cudaStream_t>(stream));
+}
+
+int tfft_batch_execute(tfft_batch b, void* stream) {
+  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+  return batch_launch(b, static_cast<cudaStream_t>(stream));
+}
+
+int tfft_batch_num_items(tfft_batch b, int64_t* items, int* segments) {
+  if (!b || !items || !segments) return fail(TFFT_EINVAL, "NULL argument");
+  *items = b->nitems;
+  *segments = (int)b->segs.size();
+  return TFFT_OK;
+}
+
+int tfft_batch_variant(tfft_batch b, int kind, int L, int* variant) {
+  if (!b || !variant) return fail(TFFT_EINVAL, "NULL argument");
+  auto it = b->choice.find({kind, L});
+  if (it == b->choice.end()) return fail(TFFT_EINVAL, "no pass of that kind and length in the batch");
+  *variant = it->second;
+  return TFFT_OK;
+}
+
+int tfft_batch_autotune(tfft_batch b, int reps, void* stream) {
+  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (reps < 1) reps = 3;
+  // cached choices: lines "kind L variant" in $TFFT_AUTOTUNE_CACHE
+  const char* cache = std::getenv("TFFT_AUTOTUNE_CACHE");
+  std::map<std::pair<int, int>, int> cached;
+  if (cache) {
+    if (FILE* f = std::fopen(cache, "r")) {
+      int k, l, v;
+      while (std::fscanf(f, "%d %d %d", &k, &l, &v) == 3) cached[{k, l}] = v;
+      std::fclose(f);
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(TFFT_ECUDA, "cudaEventCreate");
+  int rc = TFFT_OK;
+  for (auto& kv : b->choice) {
+    const std::vector<int> cands = batch_candidates(kv.first.first, kv.first.second);
+    auto hit = cached.find(kv.first);
+    if (hit != cached.end() && std::find(cands.begin(), cands.end(), hit->second) != cands.end()) {
+      kv.second = hit->second;
+      continue;
+    }
+    if (cands.size() < 2) continue;
+    float best = 1e30f;
+    int best_v = kv.second;
+    for (int v : cands) {
+      kv.second = v;
+      if ((rc = batch_upload(b, st))) break;
+      if ((rc = batch_launch(b, st))) break;  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && !rc; ++r) rc = batch_launch(b, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    kv.second = best_v;
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (cache) {
+    if (FILE* f = std::fopen(cache, "w")) {
+      for (auto& kv : b->choice) std::fprintf(f, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+      std::fclose(f);
+    }
+  }
+  return batch_upload(b, st);
+}
+
+int tfft_batch_set_wait_limit(tfft_batch b, long long cycles) {
+  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+  b->spin_limit = cycles > 0 ? cycles : 4000000000LL;
+  return TFFT_OK;
+}
+
+int tfft_batch_device_status(tfft_batch b, int* status, int reset, void* stream) {
+  if (!b || !status) return fail(TFFT_EINVAL, "NULL argument");
+  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, b->d_state, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && reset) {
+    const int zero = 0;
+    e = cudaMemcpyAsync(b->d_state, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "reading the batch status word");
+  *status = v;
+  return TFFT_OK;
 }
 
 }  // extern "C"

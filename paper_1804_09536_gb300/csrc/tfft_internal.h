@@ -25,6 +25,7 @@ struct ContigArgs {
   int sign;
   float scale;
   int* status;       // device status word
+  uint32_t wait_limit;  // polls of a bounded copy wait (TMA passes)
 };
 
 // Real-to-complex (dir -1) or complex-to-real (dir +1) along the innermost
@@ -68,6 +69,7 @@ struct StridedArgs {
   int sign;
   float scale;
   int* status;            // device status word
+  uint32_t wait_limit;    // polls of a bounded copy wait (TMA passes)
 };
 
 // Tile geometry of one stage layout seen as the 5-D array
@@ -108,6 +110,36 @@ cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s);
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
 cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
+
+// Batched persistent executor (tfft_batch.cu).  One segment = the tiles of
+// one pass of one transform; items are numbered consecutively over the
+// segments (pass-major order).
+struct BatchSeg {
+  int kind;         // 0 contiguous, 1 strided
+  int variant;      // executor tile variant
+  int prev;         // segment that must be complete first (-1: none)
+  int transform;
+  int64_t first;    // first item of the segment
+  int64_t ntiles;
+  ContigArgs ca;
+  StridedArgs sa;
+};
+
+struct BatchArgs {
+  const BatchSeg* segs;
+  int nsegs;
+  int64_t nitems;
+  unsigned long long* head;  // next item (zeroed before each launch)
+  int* done;                 // completed tiles per segment (zeroed before each launch)
+  int* abort;                // raised when a wait expires (zeroed before each launch)
+  int* status;               // device status word
+  long long spin_limit;      // clock cycles a wait may last
+};
+
+bool batch_variant(int id, int& kind, int& L, int& E, int& BW, AxisPlan& ap);
+int batch_num_variants();
+int batch_grid();
+cudaError_t launch_batch(const BatchArgs& b, int grid, cudaStream_t s);
 
 // Spectral-weight loss pieces (tfft_pointwise.cu).  The reduction uses
 // `nparts` doubles of plan-state scratch.

@@ -7,220 +7,29 @@
 #include <type_traits>
 
 #include "tfft_internal.h"
+#include "tfft_tiles.cuh"
 
 namespace tfft {
 
 namespace {
 
-template <int S, int... Rs>
-__host__ __device__ constexpr int radix_at() {
-  constexpr int r[] = {Rs...};
-  return r[S];
-}
-
-template <int S, int... Rs>
-__host__ __device__ constexpr int span_at() {
-  constexpr int r[] = {Rs...};
-  int p = 1;
-  for (int i = 0; i < S; ++i) p *= r[i];
-  return p;
-}
-
-template <int I, int N, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + 1, N>(f);
-  }
-}
-
-// Twiddle (stage span Ns > 1) and size-R butterflies of a thread's work items.
-template <int L, int E, int R, int Ns>
-__device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2* __restrict__ tw) {
-  constexpr int T = L / E;
-#pragma unroll
-  for (int q = 0; q < E / R; ++q) {
-    if constexpr (Ns > 1) {
-      const int j = jt + q * T;
-      const int step = (j % Ns) * (L / (Ns * R));
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], __ldg(&tw[r * step]));
-    }
-    Dft<R>::run(&v[q * R]);
-  }
-}
-
-// threadIdx re-read inside a loop body, opaque to the compiler: it keeps the
-// per-thread shared-memory addresses from being hoisted out of the tile loop
-// (and held in registers across it).
-__device__ __forceinline__ int opaque_tid_x() {
-  int v;
-  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(v));
-  return v;
-}
-__device__ __forceinline__ int opaque_tid_y() {
-  int v;
-  asm volatile("mov.u32 %0, %%tid.y;" : "=r"(v));
-  return v;
-}
-
-// CTAs per SM the register budget is sized for: `target` resident threads
-// (half that for the 20-element plans, whose butterflies need more registers).
-__host__ __device__ constexpr int min_blocks(int E, int threads, int target) {
-  const int t = (E >= 20 ? target / 2 : target) / threads;
-  return t > 1 ? t : (E >= 32 && threads <= 256 ? 2 : 1);
-}
-
-// Synchronises the threads of one line: a warp (or part of one) when a line
-// has at most 32 threads, the whole CTA otherwise.
-template <int T>
-__device__ __forceinline__ void line_sync() {
-  if constexpr (T <= 32) {
-    __syncwarp();
-  } else {
-    __syncthreads();
-  }
-}
-
-// Padded position inside a contiguous line: one spare slot every 8 elements
-// keeps the stride-R Stockham writes free of shared-memory bank conflicts.
-__device__ __forceinline__ int cpad(int pos) { return pos + (pos >> 3); }
-
-// ------------------------------------------------------------ contiguous lines
+using namespace tiles;
 
 template <int L, int E, int B, int... Rs>
 __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     k_contig_spec(const ContigArgs a) {
-  constexpr int T = L / E, NST = sizeof...(Rs);
-  constexpr int LP = L + L / 8;
   extern __shared__ float2 smem[];
-  const int ly = threadIdx.y;
-  float2* sl = smem + ly * LP;
-  const bool inv = a.sign > 0;
-  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
-    const int64_t line = base + ly;
-    const bool act = line < a.nlines;
-    const float2* src = a.in + line * L;
-    float2* dst = a.out + line * L;
-    const int jt = opaque_tid_x();
-    float2 v[E];
-    static_for<0, NST>([&](auto S) {
-      constexpr int s = decltype(S)::value;
-      constexpr int R = radix_at<s, Rs...>();
-      constexpr int Ns = span_at<s, Rs...>();
-      if constexpr (s == 0) {
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            float2 x = act ? src[jt + q * T + r * (L / R)] : make_float2(0.f, 0.f);
-            if (inv) x.y = -x.y;
-            v[q * R + r] = x;
-          }
-      } else {
-        constexpr int Rp = radix_at<s - 1, Rs...>();
-        constexpr int Nsp = Ns / Rp;
-        line_sync<T>();
-#pragma unroll
-        for (int q = 0; q < E / Rp; ++q)
-#pragma unroll
-          for (int r = 0; r < Rp; ++r) sl[cpad(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
-        line_sync<T>();
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = sl[cpad(jt + q * T + r * (L / R))];
-      }
-      spec_stage<L, E, R, Ns>(v, jt, a.tw);
-    });
-    constexpr int RL = radix_at<NST - 1, Rs...>();
-#pragma unroll
-    for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        float2 x = cscale(v[q * RL + r], a.scale);
-        if (inv) x.y = -x.y;
-        if (act) dst[jt + q * T + r * (L / RL)] = x;
-      }
-  }
+  for (int64_t tile = blockIdx.x; tile * B < a.nlines; tile += gridDim.x)
+    contig_tile<L, E, B, false, Rs...>(a, tile, smem, opaque_tid_x(), threadIdx.y);
 }
-
-// ------------------------------------------------------------ strided lines
 
 template <int L, int E, int W, int... Rs>
 __global__ void __launch_bounds__(W * (L / E), min_blocks(E, W * (L / E), 1024))
     k_strided_spec(const StridedArgs a) {
-  constexpr int T = L / E, NST = sizeof...(Rs);
   extern __shared__ float2 smem[];
-  int* rin = reinterpret_cast<int*>(smem + L * W);
-  int* rout = rin + L;
-  const int cx = threadIdx.x;
-  const int tid = threadIdx.y * W + cx;
-  const bool inv = a.sign > 0;
   const int64_t ntiles = a.nouter * a.ncolblocks;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t o = tile / a.ncolblocks;
-    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
-    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
-    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
-    __syncthreads();  // the previous tile is done with the row tables
-    for (int i = tid; i < L; i += W * T) {
-      int64_t g[MAXD];
-#pragma unroll
-      for (int m = 0; m < MAXD; ++m)
-        g[m] = (m == a.axis) ? (int64_t)i
-             : (m == a.d - 1) ? (int64_t)blk.x
-             : (m == a.oax0) ? go0
-             : (m == a.oax1) ? go1
-                             : 0;
-      rin[i] = (int)layout_addr(a.lin, g[0], g[1], g[2], g[3]);
-      rout[i] = (int)layout_addr(a.lout, g[0], g[1], g[2], g[3]);
-    }
-    __syncthreads();
-    const bool act = cx < blk.y;
-    const int jt = opaque_tid_y();
-    float2 v[E];
-    static_for<0, NST>([&](auto S) {
-      constexpr int s = decltype(S)::value;
-      constexpr int R = radix_at<s, Rs...>();
-      constexpr int Ns = span_at<s, Rs...>();
-      if constexpr (s == 0) {
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int pos = jt + q * T + r * (L / R);
-            float2 x = act ? a.in[rin[pos] + cx] : make_float2(0.f, 0.f);
-            if (inv) x.y = -x.y;
-            v[q * R + r] = x;
-          }
-      } else {
-        constexpr int Rp = radix_at<s - 1, Rs...>();
-        constexpr int Nsp = Ns / Rp;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < E / Rp; ++q)
-#pragma unroll
-          for (int r = 0; r < Rp; ++r)
-            smem[stockham_out_index(jt + q * T, Nsp, Rp, r) * W + cx] = v[q * Rp + r];
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = smem[(jt + q * T + r * (L / R)) * W + cx];
-      }
-      spec_stage<L, E, R, Ns>(v, jt, a.tw);
-    });
-    constexpr int RL = radix_at<NST - 1, Rs...>();
-#pragma unroll
-    for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        float2 x = cscale(v[q * RL + r], a.scale);
-        if (inv) x.y = -x.y;
-        if (act) a.out[rout[jt + q * T + r * (L / RL)] + cx] = x;
-      }
-  }
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    strided_tile<L, E, W, false, Rs...>(a, tile, smem, threadIdx.x, opaque_tid_y(), threadIdx.y * W + threadIdx.x);
 }
 
 // ------------------------------------------------------------ real lines

@@ -151,7 +151,7 @@ __device__ __forceinline__ int opaque_tid_y() {
   return v;
 }
 
-constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait is declared stuck
+constexpr uint32_t kWaitLimit = 1u << 22;  // polls of the second, clean-up wait
 
 // Coordinates of op k of a tile in one stage layout (see TmaGeo).
 __device__ __forceinline__ void tile_coords(const TmaGeo& G, int axis, int k, int64_t col, int64_t gt,
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
       issue_load(next, smem + bn * BUF, &bars[bn]);
     }
     bool ok = true;
-    if (!mbar_wait(&bars[b], (it / 3) & 1, kWaitLimit)) ok = false;
+    if (!mbar_wait(&bars[b], (it / 3) & 1, a.wait_limit)) ok = false;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__((L / E) * B, 1)
       issue(next, nxt, &bars[(it + 1) & 1]);
     }
     bool ok = true;
-    if (!mbar_wait(&bars[it & 1], (it >> 1) & 1, kWaitLimit)) ok = false;
+    if (!mbar_wait(&bars[it & 1], (it >> 1) & 1, a.wait_limit)) ok = false;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);

@@ -218,6 +218,10 @@ class Plan:
             out.append((buf.value.decode(), nb.value))
         return out
 
+    def set_wait_limit(self, polls: int):
+        """Polls of a TMA copy wait before it gives up (0: default); for error-path tests."""
+        call("tfft_plan_set_wait_limit", self._h, int(polls))
+
     def set_launch_events(self, events):
         """Record torch.cuda.Event objects around every launch of later executes."""
         if not events:
@@ -251,3 +255,95 @@ class Plan:
             sl = tuple(slice(a, a + k) for a, k in zip(st, sz))
             out[sl] = buf[off:off + n].reshape(sz)
         return out
+
+
+class Batch:
+    """Many independent transforms (one direction) run by one persistent launch.
+
+    ``plans``: bound complex-to-complex Plans.  Inputs / outputs / workspaces are
+    allocated here unless given (one stage buffer each; ``keep_input=False``
+    lets each input serve as its transform's scratch).  ``execute()`` is one
+    memset plus one kernel launch, so ``graph()`` can capture it.
+    """
+
+    def __init__(self, plans, sign: int = -1, ins=None, outs=None, works=None, keep_input: bool = True):
+        self.plans = list(plans)
+        self.sign = sign
+        dev = self.plans[0].device
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        call("tfft_batch_create", ctypes.byref(h), n, arr, sign)
+        self._h = h
+        self.ins = ins if ins is not None else [
+            p.empty_stage(0 if sign < 0 else p.g) for p in self.plans]
+        self.outs = outs if outs is not None else [
+            p.empty_stage(p.g if sign < 0 else 0) for p in self.plans]
+        if works is None:
+            works = [p.workspace("fused", True) if keep_input else None for p in self.plans]
+            # each transform needs its own workspace (they run concurrently)
+            works = [None if w is None else torch.empty_like(w) for w in works]
+        self.works = works
+        nb = ctypes.c_size_t()
+        call("tfft_batch_state_bytes", self._h, ctypes.byref(nb))
+        self.state = torch.empty(max(256, nb.value), dtype=torch.uint8, device=dev)
+        self._bind()
+
+    def _bind(self, stream=None):
+        n = len(self.plans)
+        ins = (ctypes.c_void_p * n)(*[t.data_ptr() for t in self.ins])
+        outs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in self.outs])
+        works = (ctypes.c_void_p * n)(*[0 if w is None else w.data_ptr() for w in self.works])
+        call("tfft_batch_bind", self._h, _ptr(self.state), self.state.numel(), ins, outs, works,
+             _stream_ptr(stream))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.load().tfft_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def execute(self, stream=None):
+        call("tfft_batch_execute", self._h, _stream_ptr(stream))
+
+    def autotune(self, reps: int = 3, stream=None):
+        call("tfft_batch_autotune", self._h, int(reps), _stream_ptr(stream))
+
+    def num_items(self):
+        items = ctypes.c_int64()
+        segs = ctypes.c_int()
+        call("tfft_batch_num_items", self._h, ctypes.byref(items), ctypes.byref(segs))
+        return items.value, segs.value
+
+    def variant(self, kind: int, L: int) -> int:
+        v = ctypes.c_int()
+        call("tfft_batch_variant", self._h, kind, L, ctypes.byref(v))
+        return v.value
+
+    def set_wait_limit(self, cycles: int):
+        call("tfft_batch_set_wait_limit", self._h, int(cycles))
+
+    def device_status(self, reset: bool = False, stream=None) -> int:
+        v = ctypes.c_int()
+        call("tfft_batch_device_status", self._h, ctypes.byref(v), int(reset), _stream_ptr(stream))
+        return v.value
+
+    def graph(self):
+        """A torch.cuda.CUDAGraph holding one execute (replay() runs the batch)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.execute(s)          # warm-up outside the capture (lazy CUDA set-up)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.execute()
+        return g

@@ -1,0 +1,115 @@
+"""GPU: the batched persistent executor (many transforms, one launch) (needs a GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dft, redistribute as R
+from paper_1804_09536_gb300 import inputs
+from gpu_util import RTOL_FP32, bits, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [((64, 64, 32), (1, 2)), ((64, 96, 64), (2, 2)), ((96, 64, 128), (2, 4)),
+         ((128, 64, 32), (2, 2)), ((64, 160, 96), (1, 2)), ((160, 64, 64), (2, 4)),
+         ((64, 128, 256), (2, 4)), ((256, 64, 64), (2, 2))]
+
+
+def _plans(problems, dev):
+    from paper_1804_09536_gb300.plan import Plan
+    return [Plan(s, g, device=dev) for s, g in problems]
+
+
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_batch_vs_oracle_and_standalone(cuda_device, sign):
+    from paper_1804_09536_gb300.plan import Batch
+    plans = _plans(SMALL, cuda_device)
+    xs = []
+    for k, (shape, grid) in enumerate(SMALL):
+        x = inputs.uniform_complex(shape, seed=100 + k).numpy()
+        xs.append(x)
+    b = Batch(plans, sign=sign)
+    for k, (shape, grid) in enumerate(SMALL):
+        st = 0 if sign < 0 else len(grid)
+        b.ins[k].copy_(to_dev(R.scatter(xs[k], grid, st), cuda_device))
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    for k, (shape, grid) in enumerate(SMALL):
+        g = len(grid)
+        p = plans[k]
+        if sign < 0:
+            want = dft.distributed_forward(R.scatter(xs[k], grid, 0).astype(np.complex128), shape, grid)
+            solo = p.forward(b.ins[k])
+        else:
+            want = dft.distributed_backward(R.scatter(xs[k], grid, g).astype(np.complex128), shape, grid)
+            solo = p.inverse(b.ins[k])
+        got = b.outs[k].cpu().numpy()
+        assert rel_l2(got, want) <= RTOL_FP32, (k, shape, grid)
+        # default executor tiles run the standalone passes' radices: identical bits
+        assert np.array_equal(bits(b.outs[k]), bits(solo)), (k, shape, grid)
+        torch.cuda.synchronize()
+
+
+def test_batch_48_graph_and_autotune(cuda_device):
+    """The 48-transform workload: one persistent launch per direction, captured in a
+    CUDA graph and replayed; autotuned tiles stay within the FP32 tolerance."""
+    from paper_1804_09536_gb300.plan import Batch
+    problems = inputs.batch_problems(48, seed=0)
+    plans = _plans(problems, cuda_device)
+    b = Batch(plans, sign=-1)
+    for k, (shape, grid) in enumerate(problems):
+        b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(shape, seed=k).to(cuda_device), 0))
+    g = b.graph()
+    for o in b.outs:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    refs = [plans[k].forward(b.ins[k]) for k in range(len(problems))]
+    torch.cuda.synchronize()
+    for k in range(len(problems)):
+        assert torch.equal(b.outs[k], refs[k]), k
+    items, segs = b.num_items()
+    assert segs == 3 * len(problems) and items > 0
+    b.autotune(reps=2)
+    b.execute()
+    torch.cuda.synchronize()
+    for k in range(len(problems)):
+        assert rel_l2(b.outs[k].cpu().numpy(), refs[k].cpu().numpy()) <= RTOL_FP32, k
+
+
+def test_batch_wait_expiry_reports_status(cuda_device):
+    """A forced, tiny wait limit makes a pass give up on its predecessor: the
+    launch stops and the status word says so (no fault, the context stays usable)."""
+    from paper_1804_09536_gb300.plan import Batch
+    plans = _plans(SMALL[:3], cuda_device)
+    b = Batch(plans, sign=-1)
+    b.set_wait_limit(1)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status(reset=True) == 1
+    b.set_wait_limit(0)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    ref = plans[0].forward(b.ins[0])
+    assert torch.equal(b.outs[0], ref)
+
+
+def test_tma_wait_expiry_reports_status(cuda_device):
+    """Same for the TMA passes: one poll per copy wait cannot see the copy land."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (256, 128, 256), (2, 4)
+    p = Plan(shape, grid, device=cuda_device)
+    assert any("tma" in n for n, _ in p.launch_info(-1))
+    x = p.scatter(inputs.uniform_complex(shape, seed=1).to(cuda_device), 0)
+    p.set_wait_limit(1)
+    p.forward(x)
+    torch.cuda.synchronize()
+    assert p.device_status(reset=True) == 1
+    p.set_wait_limit(0)
+    y = p.forward(x)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    pp = Plan(shape, grid, device=cuda_device, tma=False)
+    assert torch.equal(y, pp.forward(x))
