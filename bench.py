@@ -247,6 +247,11 @@ def run_ours(args):
     r2c = r2c_slab(plan_cls=Plan, dev=dev, steps=max(5, min(args.steps, 50)), barrier=barrier,
                    tma=not args.no_tma)
 
+    # the differentiable 512^3 workload: loss = sum |F(x) w|^2 and its gradient
+    ag = autograd_step(plan, x, dev, steps=max(3, min(args.steps, 20)), barrier=barrier)
+    # the batch of 48 uneven transforms: one persistent launch in a CUDA graph
+    bt = batch48(dev, steps=max(3, min(args.steps, 20)), barrier=barrier, autotune=not args.no_autotune)
+
     # end to end through the public API with host buffers: pinned H2D of the
     # input, forward + inverse, D2H of the result, every step
     h_in = x.cpu().pin_memory()
@@ -315,6 +320,8 @@ def run_ours(args):
                                    "packed": round(extra["packed"], 4)},
         "fused_vs_packed_speedup": round(extra["packed"] / ms_step, 3),
         "r2c_slab_256": r2c,
+        "autograd_512": ag,
+        "batch48": bt,
         "e2e": {"value": round(world * FLOP_PER_STEP / (e2e_ms * 1e-3) / 1e9, 2), "unit": UNIT,
                 "ms_per_step": round(e2e_ms, 4),
                 "h2d_bytes_per_step": h_in.numel() * h_in.element_size(),
@@ -373,6 +380,104 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True):
             "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
             "note": "c2r overwrites its input; the forward output is reused as the inverse's input"}
+
+
+def autograd_step(plan, x, dev, steps, barrier):
+    """loss = sum |F(x) w|^2 (w seeded U[0,1) on the spectrum) and its gradient via the
+    adjoint, through torch.autograd; ms per loss + backward step."""
+    import torch
+    from paper_1804_09536_gb300 import inputs
+    from paper_1804_09536_gb300.autograd import spectral_weight_loss
+    w = plan.scatter(inputs.uniform01_real(SHAPE, seed=1).to(dev), plan.g)
+    xr = x.clone().requires_grad_(True)
+
+    def one():
+        xr.grad = None
+        loss = spectral_weight_loss(xr, w, plan)
+        loss.backward()
+        return loss
+    for _ in range(2):
+        one()
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        one()
+    b.record()
+    barrier()
+    ms = a.elapsed_time(b) / steps
+    n = math.prod(SHAPE)
+    # algorithmic bytes: forward 3 sweeps (2 x 8 B), loss (read y 8 B + w 4 B), seed (read y, w,
+    # write z: 20 B), adjoint 3 sweeps
+    nbytes = n * (6 * 16 + 12 + 20)
+    peak, _ = _peaks()
+    return {"workload": "512^3 c2c pencil 4x8: loss = sum |F(x) w|^2, w U[0,1) seed 1; forward + loss "
+                        "+ gradient (adjoint transform) via torch.autograd",
+            "ms_per_step": round(ms, 4), "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+            "algorithmic_bytes": nbytes}
+
+
+def batch48(dev, steps, barrier, autotune=True):
+    """48 transforms drawn from the uneven-shape set: one persistent launch per
+    forward, replayed from a CUDA graph, vs the same transforms launched plan by plan."""
+    import torch
+    from paper_1804_09536_gb300 import inputs
+    from paper_1804_09536_gb300.plan import Batch, Plan
+    problems = inputs.batch_problems(48, seed=0)
+    plans = [Plan(sh, gr, device=dev) for sh, gr in problems]
+    b = Batch(plans, sign=-1)
+    for k, (sh, gr) in enumerate(problems):
+        b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(sh, seed=k).to(dev), 0))
+    if autotune:
+        x_keep = [t.clone() for t in b.ins]
+        b.autotune(reps=3)
+        for t, k in zip(b.ins, x_keep):
+            t.copy_(k)
+    g = b.graph()
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        e.record()
+        barrier()
+        return a.elapsed_time(e) / steps
+    ms_graph = timed(g.replay)
+    works = [p.workspace("fused", True) for p in plans]
+
+    def per_plan():
+        for k, p in enumerate(plans):
+            p.execute(-1, b.ins[k], b.outs[k], "fused", works[k])
+    ms_plans = timed(per_plan)
+    nsum = sum(math.prod(sh) for sh, _ in problems)
+    flops = sum(5.0 * math.prod(sh) * math.log2(math.prod(sh)) for sh, _ in problems)
+    nbytes = 3 * 16 * nsum
+    peak, _ = _peaks()
+    items, segs = b.num_items()
+    return {"workload": "48 c2c complex64 transforms, shapes drawn (seed 0) from {64^3, 96^3, 128^3, "
+                        "64x128x256, 160^3, 256^3}, grids from {1x2, 2x2, 2x4}; forward",
+            "elements": nsum, "items": items, "segments": segs,
+            "graph_ms": round(ms_graph, 4), "per_plan_ms": round(ms_plans, 4),
+            "speedup_vs_per_plan": round(ms_plans / ms_graph, 3),
+            "GFLOPs": round(flops / (ms_graph * 1e-3) / 1e9, 1),
+            "hbm_frac": round(nbytes / (ms_graph * 1e-3) / 1e9 / peak, 4),
+            "autotuned": bool(autotune),
+            "variants": {f"{'contig' if k == 0 else 'strided'}_{L}": b.variant(k, L)
+                         for k in (0, 1) for L in (64, 96, 128, 160, 256) if _has_variant(b, k, L)}}
+
+
+def _has_variant(b, kind, L):
+    try:
+        b.variant(kind, L)
+        return True
+    except Exception:
+        return False
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -450,6 +555,7 @@ def main():
     ap.add_argument("--grid", type=int, nargs="*", default=list(GRID))
     ap.add_argument("--no-tma", action="store_true",
                     help="plain load/store passes only (comparison and profiling)")
+    ap.add_argument("--no-autotune", action="store_true", help="batch executor with default tiles")
     ap.add_argument("--profile-only", action="store_true",
                     help="headline loop only (no comparison paths, e2e or CPU baseline)")
     args = ap.parse_args()

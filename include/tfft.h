@@ -64,7 +64,10 @@ typedef struct tfft_plan_s *tfft_plan;
 
 enum { TFFT_FORWARD = -1, TFFT_BACKWARD = +1 };
 enum { TFFT_C2C = 0, TFFT_R2C = 1 };
-enum { TFFT_FP32 = 0 };
+/* precision: FP32 butterflies everywhere, or the radix-16 stage of length-512
+   contiguous passes on the tensor cores with split hi/lo BF16 or FP16 operands
+   and FP32 accumulation (other passes stay FP32) */
+enum { TFFT_FP32 = 0, TFFT_TC_BF16X3 = 1, TFFT_TC_FP16X3 = 2 };
 /* plan flags */
 enum {
   TFFT_NORM_FORWARD = 0,
@@ -108,7 +111,8 @@ int tfft_decompose(int64_t N, int64_t M, int64_t p, int64_t *n, int64_t *s);
  * grid_ndims-D virtual process grid grid[0..grid_ndims-1] (Sec. 3.4; the grid
  * is taken as given, no dims-create balancing).  kind: TFFT_C2C or TFFT_R2C
  * (real input, Hermitian half on the last axis; N[d-1] even).  precision:
- * TFFT_FP32.  flags: TFFT_NORM_FORWARD or TFFT_NORM_BACKWARD.
+ * TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3.  flags: TFFT_NORM_FORWARD or
+ * TFFT_NORM_BACKWARD, optionally | TFFT_NO_TMA.
  * Transforms need every length to factor into 2, 3 and 5 and be <= 4096;
  * a plan with other lengths is still created and redistributes, but its
  * tfft_execute() and tfft_partial() return TFFT_EUNSUPPORTED.

@@ -18,6 +18,8 @@ TFFT_BACKWARD = 1
 TFFT_C2C = 0
 TFFT_R2C = 1
 TFFT_FP32 = 0
+TFFT_TC_BF16X3 = 1
+TFFT_TC_FP16X3 = 2
 TFFT_NORM_FORWARD = 0
 TFFT_NORM_BACKWARD = 4
 TFFT_NO_TMA = 8

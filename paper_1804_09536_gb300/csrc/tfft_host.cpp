@@ -737,7 +737,9 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
     a.status = reinterpret_cast<int*>(p->d_state);
     a.wait_limit = p->wait_limit;
-    if (a.ap.tma && p->use_tma)
+    if (p->precision != TFFT_FP32 && tc_supported(a.ap.L))
+      e = launch_contig_tc(a, p->precision, st);
+    else if (a.ap.tma && p->use_tma)
       e = launch_contig_tma(a, st);
     else
       e = launch_contig(a, st);
@@ -874,7 +876,8 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     return fail(TFFT_EINVAL, "grid_ndims must be 0..min(3, ndims - 1) (Sec. 3.6)");
   if (grid_ndims > 0 && !grid) return fail(TFFT_EINVAL, "grid is NULL");
   if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
-  if (precision != TFFT_FP32) return fail(TFFT_EUNSUPPORTED, "precision must be TFFT_FP32");
+  if (precision != TFFT_FP32 && precision != TFFT_TC_BF16X3 && precision != TFFT_TC_FP16X3)
+    return fail(TFFT_EINVAL, "precision must be TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3");
   if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA)) return fail(TFFT_EINVAL, "unknown flag bits");
   auto p = new tfft_plan_s();
   p->d = ndims;
@@ -1176,7 +1179,9 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
   } else {
     const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
     const bool tma = (s.kind == S_CONTIG) ? (ap.tma && p->use_tma) : s.tma;
-    nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") + (tma ? "_tma" : "") +
+    const bool tc = s.kind == S_CONTIG && p->precision != TFFT_FP32 && tc_supported(ap.L);
+    nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
+         (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : tma ? "_tma" : "") +
          (ap.spec ? "_L" + std::to_string(ap.L) : ap.E == 0 ? std::string("_generic")
                                                             : "_E" + std::to_string(ap.E));
     elems = p->nelems;

@@ -141,6 +141,11 @@ int batch_num_variants();
 int batch_grid();
 cudaError_t launch_batch(const BatchArgs& b, int grid, cudaStream_t s);
 
+// Tensor-core contiguous pass (tfft_tc.cu): length 512 = 32 x 16 with the
+// radix-16 stage as split hi/lo 16-bit MMAs; precision 1 = BF16 x3, 2 = FP16 x3.
+bool tc_supported(int L);
+cudaError_t launch_contig_tc(const ContigArgs& a, int precision, cudaStream_t s);
+
 // Spectral-weight loss pieces (tfft_pointwise.cu).  The reduction uses
 // `nparts` doubles of plan-state scratch.
 constexpr int kReductionParts = 1024;

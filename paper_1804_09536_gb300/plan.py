@@ -38,7 +38,7 @@ class Plan:
     """
 
     def __init__(self, shape, grid, kind: str = "c2c", norm: str = "forward", device=None,
-                 bind: bool = True, tma: bool = True):
+                 bind: bool = True, tma: bool = True, precision: str = "fp32"):
         self.shape = tuple(int(n) for n in shape)
         self.grid = tuple(int(m) for m in grid)
         self.kind = kind
@@ -49,8 +49,10 @@ class Plan:
         h = ctypes.c_void_p()
         shp = (ctypes.c_int64 * len(self.shape))(*self.shape)
         grd = (ctypes.c_int * max(1, len(self.grid)))(*(self.grid or (1,)))
+        prec = {"fp32": _lib.TFFT_FP32, "bf16x3": _lib.TFFT_TC_BF16X3, "fp16x3": _lib.TFFT_TC_FP16X3}[precision]
+        self.precision = precision
         call("tfft_plan_create", ctypes.byref(h), len(self.shape), shp, len(self.grid), grd,
-             kind_id, _lib.TFFT_FP32, flags)
+             kind_id, prec, flags)
         self._h = h
         self.d = len(self.shape)
         self.g = len(self.grid)

@@ -1,0 +1,50 @@
+"""GPU: tensor-core radix-16 stage (split hi/lo BF16 / FP16, FP32 accumulate) (needs a GPU).
+
+The error of these modes is reported against the FP64 oracle; the bars below
+are the measured error with headroom (BF16 x3 keeps about 16 mantissa bits,
+FP16 x3 about 22), not the FP32 1e-5 bar.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dft, redistribute as R
+from paper_1804_09536_gb300 import inputs
+from gpu_util import RTOL_FP32, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+BARS = {"bf16x3": 2e-5, "fp16x3": 1e-6}   # measured on 8 x 16 x 512: 3.1e-6, 2.7e-7
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("shape,grid", [((8, 16, 512), (2, 2)), ((32, 24, 512), (4, 8)), ((4, 4, 512), ())])
+def test_tc_forward_inverse_vs_oracle(cuda_device, precision, shape, grid):
+    from paper_1804_09536_gb300.plan import Plan
+    g = len(grid)
+    x = inputs.normal_complex(shape, seed=0).numpy()
+    p = Plan(shape, grid, device=cuda_device, precision=precision)
+    assert any("_tc_" in n for n, _ in p.launch_info(-1))
+    b0 = R.scatter(x, grid, 0)
+    y = p.forward(to_dev(b0, cuda_device))
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    want = dft.distributed_forward(b0.astype(np.complex128), shape, grid)
+    err_f = rel_l2(y.cpu().numpy(), want)
+    z = p.inverse(y.clone())
+    err_b = rel_l2(z.cpu().numpy(), b0)
+    assert err_f <= BARS[precision], err_f
+    assert err_b <= 2 * BARS[precision], err_b
+    # the FP32 path on the same input for comparison
+    yf = Plan(shape, grid, device=cuda_device).forward(to_dev(b0, cuda_device))
+    assert rel_l2(yf.cpu().numpy(), want) <= RTOL_FP32
+
+
+def test_tc_partial_tiles(cuda_device):
+    """Lines that do not fill the last 8-line tile."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape = (3, 5, 512)
+    x = inputs.normal_complex(shape, seed=3).numpy()
+    p = Plan(shape, (), device=cuda_device, precision="fp16x3")
+    y = p.forward(to_dev(x.reshape(-1), cuda_device))
+    assert rel_l2(y.cpu().numpy(), dft.fftn_forward(x.astype(np.complex128)).reshape(-1)) <= BARS["fp16x3"]
