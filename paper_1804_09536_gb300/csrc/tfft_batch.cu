@@ -48,27 +48,40 @@ __device__ __forceinline__ void run_tile(const BatchSeg& S, int64_t tile, float2
     strided_tile<L, E, BW, true, Rs...>(S.sa, tile, smem, tid % BW, tid / BW, tid);
 }
 
+// Segments whose first-item table fits shared memory use it for the lookup.
+constexpr int kSmemSegs = 1024;
+
 __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const BatchArgs b) {
   extern __shared__ float2 smem[];
+  __shared__ long long s_first[kSmemSegs];
   __shared__ long long s_item;
   __shared__ int s_seg;
   __shared__ int s_abort;
   const int tid = threadIdx.x;
+  const bool seg_in_smem = b.nsegs <= kSmemSegs;
+  if (seg_in_smem)
+    for (int i = tid; i < b.nsegs; i += kBatchThreads) s_first[i] = b.segs[i].first;
+  // items are taken one ahead: the next one is claimed while the current one runs
+  long long next = 0;
+  if (tid == 0) next = (long long)atomicAdd(b.head, 1ull);
+  __syncthreads();
   for (;;) {
     if (tid == 0) {
-      const long long item = (long long)atomicAdd(b.head, 1ull);
+      const long long item = next;
       int seg = 0, abort = 0;
       if (item < b.nitems) {
+        next = (long long)atomicAdd(b.head, 1ull);
         int lo = 0, hi = b.nsegs - 1;
         while (lo < hi) {  // last segment whose first item <= item
           const int mid = (lo + hi + 1) >> 1;
-          if (b.segs[mid].first <= item) lo = mid;
+          const long long f = seg_in_smem ? s_first[mid] : b.segs[mid].first;
+          if (f <= item) lo = mid;
           else hi = mid - 1;
         }
         seg = lo;
         const int prev = b.segs[seg].prev;
         if (prev >= 0) {
-          const int need = (int)b.segs[prev].ntiles;
+          const int need = (int)b.segs[prev].nitems;
           const long long t0 = clock64();
           while (*(volatile int*)&b.done[prev] < need) {
             if (*(volatile int*)b.abort) {
@@ -95,16 +108,21 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const BatchArgs b) {
     const int seg = s_seg;
     if (item >= b.nitems || s_abort) break;
     const BatchSeg& S = b.segs[seg];
-    const int64_t tile = item - S.first;
-    switch (S.variant) {
+    // an item is a run of up to `per_item` consecutive tiles of one segment
+    const int64_t t0 = (item - S.first) * S.per_item;
+    const int64_t t1 = (t0 + S.per_item < S.ntiles) ? t0 + S.per_item : S.ntiles;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+      switch (S.variant) {
 #define X(ID, KIND, L, E, BW, ...)                              \
   case ID:                                                      \
     run_tile<KIND, L, E, BW, __VA_ARGS__>(S, tile, smem, tid);  \
     break;
-      TFFT_BATCH_VARIANTS(X)
+        TFFT_BATCH_VARIANTS(X)
 #undef X
-      default:
-        break;
+        default:
+          break;
+      }
+      __syncthreads();  // shared memory is free for the next tile
     }
     __threadfence();
     __syncthreads();  // every thread's stores are issued and fenced; s_item may be reused

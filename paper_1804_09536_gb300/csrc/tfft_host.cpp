@@ -1375,16 +1375,6 @@ std::vector<int> batch_candidates(int kind, int L) {
   return v;
 }
 
-int64_t batch_ntiles(tfft_plan p, const Step& s, int variant) {
-  int k, l, e, bw;
-  AxisPlan ap;
-  batch_variant(variant, k, l, e, bw, ap);
-  if (s.kind == S_CONTIG) return (s.nlines + bw - 1) / bw;
-  int64_t nouter = 1;
-  for (int m = 0; m < p->d - 1; ++m)
-    if (m != s.axis) nouter *= p->cshape[m];
-  return nouter * (int64_t)colblock_list(p, s.lin, s.lout, bw).size();
-}
 
 // Items, segment table and column blocks for the current variant choices,
 // written into the bound state buffer.
@@ -1457,8 +1447,13 @@ int batch_upload(tfft_batch b, cudaStream_t st) {
       a.status = status;
       D.ntiles = nouter * a.ncolblocks;
     }
+    // items of about 16K elements: small tiles are grouped so that the queue,
+    // the lookup and the completion fence are paid once per ~256 KB moved
+    const int64_t tile_elems = s.kind == S_CONTIG ? (int64_t)bw * s.L : (int64_t)bw * s.L;
+    D.per_item = std::max<int64_t>(1, std::min<int64_t>(16, 16384 / std::max<int64_t>(1, tile_elems)));
+    D.nitems = (D.ntiles + D.per_item - 1) / D.per_item;
     h.ntiles = D.ntiles;
-    first += D.ntiles;
+    first += D.nitems;
   }
   b->nitems = first;
   std::memcpy(img.data() + b->seg_off, dsegs.data(), dsegs.size() * sizeof(BatchSeg));

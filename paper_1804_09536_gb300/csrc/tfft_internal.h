@@ -121,6 +121,8 @@ struct BatchSeg {
   int transform;
   int64_t first;    // first item of the segment
   int64_t ntiles;
+  int64_t per_item; // tiles per work item
+  int64_t nitems;   // items of the segment = ceil(ntiles / per_item)
   ContigArgs ca;
   StridedArgs sa;
 };
@@ -130,7 +132,7 @@ struct BatchArgs {
   int nsegs;
   int64_t nitems;
   unsigned long long* head;  // next item (zeroed before each launch)
-  int* done;                 // completed tiles per segment (zeroed before each launch)
+  int* done;                 // completed items per segment (zeroed before each launch)
   int* abort;                // raised when a wait expires (zeroed before each launch)
   int* status;               // device status word
   long long spin_limit;      // clock cycles a wait may last

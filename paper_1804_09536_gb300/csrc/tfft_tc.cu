@@ -96,6 +96,18 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Shared-memory matrix descriptor: no swizzle, K-major core matrices of
 // 8 rows x 16 bytes; lbo = bytes between K-adjacent core matrices, sbo =
 // bytes between 8-row groups; descriptor version 1.
@@ -253,13 +265,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contig_tc512(const ContigArgs a
       }
       umma_commit(bar);
     }
-    // bounded wait for the MMAs
-    bool ok = false;
-    for (uint32_t i = 0; i < a.wait_limit; ++i)
-      if (mbar_try(bar, phase)) {
-        ok = true;
-        break;
-      }
+    // bounded wait for the MMAs (first poll non-blocking)
+    bool ok = mbar_test(bar, phase);
+    for (uint32_t i = 1; i < a.wait_limit && !ok; ++i) ok = mbar_try(bar, phase);
     phase ^= 1;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
@@ -291,8 +299,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_contig_tc512(const ContigArgs a
     tc_fence_after();
   }
   if (failed && tid == 0) {
-    // let the outstanding MMAs finish before their memory is released
-    for (uint32_t i = 0; i < a.wait_limit; ++i)
+    // let the outstanding MMAs finish before their tensor memory is released
+    // (a fixed, generous bound: the requested limit may have been tiny)
+    for (uint32_t i = 0; i < (1u << 22); ++i)
       if (mbar_try(bar, phase ^ 1)) break;
   }
   tc_fence_before();

@@ -48,3 +48,22 @@ def test_tc_partial_tiles(cuda_device):
     p = Plan(shape, (), device=cuda_device, precision="fp16x3")
     y = p.forward(to_dev(x.reshape(-1), cuda_device))
     assert rel_l2(y.cpu().numpy(), dft.fftn_forward(x.astype(np.complex128)).reshape(-1)) <= BARS["fp16x3"]
+
+
+def test_tc_wait_expiry_reports_status(cuda_device):
+    """A one-poll limit on the MMA-completion wait expires: status word set, TMEM
+    released, the context stays usable and a normal run afterwards is correct."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape = (16, 16, 512)
+    x = to_dev(inputs.normal_complex(shape, seed=4).numpy().reshape(-1), cuda_device)
+    p = Plan(shape, (), device=cuda_device, precision="bf16x3")
+    p.set_wait_limit(1)
+    p.forward(x)
+    torch.cuda.synchronize()
+    assert p.device_status(reset=True) == 1
+    p.set_wait_limit(0)
+    y = p.forward(x)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    want = dft.fftn_forward(x.cpu().numpy().reshape(shape).astype(np.complex128)).reshape(-1)
+    assert rel_l2(y.cpu().numpy(), want) <= BARS["bf16x3"]
