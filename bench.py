@@ -140,6 +140,22 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The slowest rank's time (MAX all-reduce over the process group; gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, flop_per_step: float, ms_per_step: float) -> float:
+    """Whole-job GFLOP/s: every replica's flops over the slowest replica's time."""
+    return world * flop_per_step / (ms_per_step * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -213,13 +229,9 @@ def run_ours(args):
                 kern.setdefault(name, {"ms": [], "bytes": nbytes})["ms"].append(evs[i].elapsed_time(evs[i + 1]))
     gpu_launches = args.steps * (nf + nb)
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world)
     ms_step = total_ms / args.steps
-    value = world * FLOP_PER_STEP / (ms_step * 1e-3) / 1e9
+    value = whole_job_value(world, FLOP_PER_STEP, ms_step)
 
     if args.profile_only:
         if rank == 0:
@@ -273,12 +285,7 @@ def run_ours(args):
         h_out.copy_(z, non_blocking=True)
     b.record(stream)
     barrier()
-    e2e_ms = a.elapsed_time(b) / esteps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / esteps, world)
     # round-trip check of the last step (the timed work really happened)
     err = float(torch.linalg.vector_norm(h_out - h_in) / torch.linalg.vector_norm(h_in))
 
