@@ -134,7 +134,7 @@ constexpr size_t batch_smem() {
   size_t m = 0;
 #define X(ID, KIND, L, E, BW, ...)                                                                     \
   {                                                                                                    \
-    const size_t v = (KIND == 0) ? (size_t)BW * (L + L / 8) * sizeof(float2)                          \
+    const size_t v = (KIND == 0) ? (size_t)BW * line_pitch<L, __VA_ARGS__>() * sizeof(float2) \
                                  : (size_t)L * BW * sizeof(float2) + 2 * (size_t)L * sizeof(int);     \
     m = v > m ? v : m;                                                                                 \
   }

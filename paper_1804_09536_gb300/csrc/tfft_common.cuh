@@ -290,7 +290,6 @@ struct AxisPlan {
   int nst;         // number of radix stages
   uint64_t code;   // radix of stage s = (code >> 5 s) & 31
   int spec;        // 1: a compile-time specialised kernel exists for this plan
-  int tma;         // 1: the contiguous pass streams lines with bulk copies
   int width;       // lines per CTA (contiguous) or tile width W (strided)
   int radix[MAXSTAGES];
 };

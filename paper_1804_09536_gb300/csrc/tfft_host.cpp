@@ -78,6 +78,7 @@ struct Step {
   int tma_E = 0, tma_W = 0;
   size_t tma_cb_off = 0;
   int64_t tma_ncb = 0;
+  bool tma_outer_fastest = false;  // tile order of the TMA pass
   TmaGeo gin{}, gout{};
 };
 
@@ -182,10 +183,9 @@ DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
 // so plans with at most 32 threads per line (W >= 16 columns) are preferred.
 bool make_axis_plan(int L, bool strided, AxisPlan& best) {
   best.spec = 0;
-  best.tma = 0;
   best.width = 0;
   if (L == 1) {
-    best = AxisPlan{1, 1, 1, 0, 0, 0, 0, 1, {}};
+    best = AxisPlan{1, 1, 1, 0, 0, 0, 1, {}};
     return true;
   }
   static const int Es[] = {8, 16, 4, 12, 20, 24, 10, 6, 15, 5, 3, 2};
@@ -308,7 +308,9 @@ std::pair<size_t, int64_t> get_colblocks(tfft_plan p, int lin, int lout, int W) 
 }
 
 // Column blocks of a (lin, lout, W) strided pass as a list (for the batch).
-std::vector<int2> colblock_list(tfft_plan p, int lin, int lout, int W) {
+// Sorted cut points of the innermost axis: 0, its length and the first
+// column of every rank of `lin` and `lout` that cut it.
+std::vector<int64_t> column_cuts(tfft_plan p, int lin, int lout) {
   const int last = p->d - 1;
   const int64_t N = p->cshape[last];
   std::vector<int64_t> cuts = {0, N};
@@ -325,6 +327,11 @@ std::vector<int2> colblock_list(tfft_plan p, int lin, int lout, int W) {
   }
   std::sort(cuts.begin(), cuts.end());
   cuts.erase(std::unique(cuts.begin(), cuts.end()), cuts.end());
+  return cuts;
+}
+
+std::vector<int2> colblock_list(tfft_plan p, int lin, int lout, int W) {
+  const std::vector<int64_t> cuts = column_cuts(p, lin, lout);
   std::vector<int2> blocks;
   for (size_t k = 0; k + 1 < cuts.size(); ++k)
     for (int64_t c = cuts[k]; c < cuts[k + 1]; c += W)
@@ -613,6 +620,10 @@ Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
       auto cbt = get_colblocks(p, lin, lout, Wt);
       s.tma_cb_off = cbt.first;
       s.tma_ncb = cbt.second;
+      // measured on 512^3, 4 x 8 grid: the axis-0 pass is faster
+      // with the outer index running fastest, the axis-1 pass with the
+      // column blocks running fastest
+      s.tma_outer_fastest = axis == 0;
     }
   }
   return s;
@@ -739,8 +750,6 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.wait_limit = p->wait_limit;
     if (p->precision != TFFT_FP32 && tc_supported(a.ap.L))
       e = launch_contig_tc(a, p->precision, st);
-    else if (a.ap.tma && p->use_tma)
-      e = launch_contig_tma(a, st);
     else
       e = launch_contig(a, st);
   } else if (s.kind == S_STRIDED) {
@@ -755,6 +764,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
     a.colblocks = reinterpret_cast<const int2*>(p->d_state + s.cb_off);
     a.ncolblocks = s.ncb;
+    a.outer_fastest = 0;
     int oax[2] = {-1, -1}, no = 0;
     int64_t nouter = 1;
     for (int m = 0; m < p->d - 1; ++m)
@@ -780,6 +790,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
         at.W = s.tma_W;
         at.colblocks = reinterpret_cast<const int2*>(p->d_state + s.tma_cb_off);
         at.ncolblocks = s.tma_ncb;
+        at.outer_fastest = s.tma_outer_fastest ? 1 : 0;
         e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
         done = true;
       }
@@ -958,11 +969,6 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     }
     int width = 0;
     if (spec_plan(L, false, p->nelems, ap, width)) ap.width = width;
-    int Ec = 0, Bc = 0;
-    if (p->use_tma && ap.spec && tma_contig_plan(L, Ec, Bc) && Ec == ap.E) {
-      ap.width = Bc;
-      ap.tma = 1;
-    }
     if (spec_plan(L, true, p->nelems, aps, width)) aps.width = width;
     p->aplan[L] = ap;
     p->aplan_s[L] = aps;
@@ -1178,7 +1184,7 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
     (void)X;
   } else {
     const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
-    const bool tma = (s.kind == S_CONTIG) ? (ap.tma && p->use_tma) : s.tma;
+    const bool tma = s.kind == S_STRIDED && s.tma;
     const bool tc = s.kind == S_CONTIG && p->precision != TFFT_FP32 && tc_supported(ap.L);
     nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
          (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : tma ? "_tma" : "") +
@@ -1429,6 +1435,7 @@ int batch_upload(tfft_batch b, cudaStream_t st) {
       std::memcpy(img.data() + cb, blocks.data(), blocks.size() * sizeof(int2));
       a.colblocks = reinterpret_cast<const int2*>(b->d_state + cb);
       a.ncolblocks = (int64_t)blocks.size();
+      a.outer_fastest = 0;
       cb += align_up(h.cb_cap * sizeof(int2), 256);
       int oax[2] = {-1, -1}, no = 0;
       int64_t nouter = 1;

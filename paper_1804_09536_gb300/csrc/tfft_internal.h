@@ -62,6 +62,7 @@ struct StridedArgs {
   const float2* tw;
   const int2* colblocks;  // (first column, width) along axis d - 1
   int64_t ncolblocks;
+  int outer_fastest;      // TMA passes: tiles go (column block, outer) instead of (outer, column block)
   int64_t nouter;
   int oax0, oax1;         // the outer axes (or -1), outer index = g[oax0] * on1 + g[oax1]
   int64_t on1;
@@ -173,9 +174,7 @@ cudaError_t launch_real_spec(const RealArgs& a, cudaStream_t s);
 // tma_strided_variant: elements per thread and tile width of the strided TMA
 // variant of length L with width want_W if compiled, else the default one.
 bool tma_strided_variant(int L, int want_W, int want_E, int& E, int& W);
-bool tma_contig_plan(int L, int& E, int& B);
 cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gin, const TmaGeo& gout,
                                const void* tmap_in, const void* tmap_out, cudaStream_t s);
-cudaError_t launch_contig_tma(const ContigArgs& a, cudaStream_t s);
 
 }  // namespace tfft

@@ -48,7 +48,8 @@ template <int L, int E, int B, int... Rs>
 __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     k_r2c_spec(const RealArgs a) {
   constexpr int T = L / E, NST = sizeof...(Rs);
-  constexpr int LP = L + L / 8;
+  constexpr int LP = line_pitch<L, Rs...>();
+  constexpr int P = pad_every<Rs...>();
   extern __shared__ float2 smem[];
   const int ly = threadIdx.y;
   float2* sl = smem + ly * LP;
@@ -75,12 +76,12 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
 #pragma unroll
         for (int q = 0; q < E / Rp; ++q)
 #pragma unroll
-          for (int r = 0; r < Rp; ++r) sl[cpad(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+          for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
         line_sync<T>();
 #pragma unroll
         for (int q = 0; q < E / R; ++q)
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = sl[cpad(jt + q * T + r * (L / R))];
+          for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
       }
       spec_stage<L, E, R, Ns>(v, jt, a.tw);
     });
@@ -89,11 +90,11 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
 #pragma unroll
     for (int q = 0; q < E / RL; ++q)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) sl[cpad(jt + q * T + r * (L / RL))] = v[q * RL + r];
+      for (int r = 0; r < RL; ++r) sl[padp<P>(jt + q * T + r * (L / RL))] = v[q * RL + r];
     line_sync<T>();
     for (int k = jt; k <= L; k += T) {
-      const float2 zk = sl[cpad(k == L ? 0 : k)];
-      const float2 zm = sl[cpad(k == 0 ? 0 : L - k)];
+      const float2 zk = sl[padp<P>(k == L ? 0 : k)];
+      const float2 zm = sl[padp<P>(k == 0 ? 0 : L - k)];
       const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));   // (Z[k] + conj Z[L-k]) / 2
       const float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));   // (Z[k] - conj Z[L-k]) / 2
       const float2 o = cmul(__ldg(&a.tw2[k]), mul_mi(d));                          // -i w^k d
@@ -106,7 +107,8 @@ template <int L, int E, int B, int... Rs>
 __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     k_c2r_spec(const RealArgs a) {
   constexpr int T = L / E, NST = sizeof...(Rs);
-  constexpr int LP = L + L / 8 + 1;
+  constexpr int LP = line_pitch<L, Rs...>() + 1;
+  constexpr int P = pad_every<Rs...>();
   extern __shared__ float2 smem[];
   const int ly = threadIdx.y;
   float2* sl = smem + ly * LP;
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     for (int k = jt; k <= L; k += T) {
       float2 x = act ? src[k] : make_float2(0.f, 0.f);
       if (k == 0 || k == L) x.y = 0.f;
-      sl[cpad(k)] = x;
+      sl[padp<P>(k)] = x;
     }
     line_sync<T>();
     float2 v[E];
@@ -134,8 +136,8 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int k = jt + q * T + r * (L / R);
-            const float2 xk = sl[cpad(k)];
-            const float2 xm = sl[cpad(L - k)];
+            const float2 xk = sl[padp<P>(k)];
+            const float2 xm = sl[padp<P>(L - k)];
             const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);      // X[k] + conj X[L-k]
             const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);      // X[k] - conj X[L-k]
             const float2 w = __ldg(&a.tw2[k]);
@@ -150,12 +152,12 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
 #pragma unroll
         for (int q = 0; q < E / Rp; ++q)
 #pragma unroll
-          for (int r = 0; r < Rp; ++r) sl[cpad(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+          for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
         line_sync<T>();
 #pragma unroll
         for (int q = 0; q < E / R; ++q)
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = sl[cpad(jt + q * T + r * (L / R))];
+          for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
       }
       spec_stage<L, E, R, Ns>(v, jt, a.tw);
     });
@@ -181,7 +183,7 @@ template <int L, int E, int B, int... Rs>
 cudaError_t run_contig(const ContigArgs& a, cudaStream_t s) {
   static cudaError_t attr = allow_smem(k_contig_spec<L, E, B, Rs...>);
   if (attr != cudaSuccess) return attr;
-  const size_t smem = (size_t)B * (L + L / 8) * sizeof(float2);
+  const size_t smem = (size_t)B * line_pitch<L, Rs...>() * sizeof(float2);
   int64_t grid = (a.nlines + B - 1) / B;
   if (grid > kMaxGrid) grid = kMaxGrid;
   if (grid < 1) return cudaSuccess;
@@ -233,12 +235,12 @@ cudaError_t run_real(const RealArgs& a, cudaStream_t s) {
   if (a.dir < 0) {
     static cudaError_t attr = allow_smem(k_r2c_spec<L, E, B, Rs...>);
     if (attr != cudaSuccess) return attr;
-    const size_t smem = (size_t)B * (L + L / 8) * sizeof(float2);
+    const size_t smem = (size_t)B * line_pitch<L, Rs...>() * sizeof(float2);
     k_r2c_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
   } else {
     static cudaError_t attr = allow_smem(k_c2r_spec<L, E, B, Rs...>);
     if (attr != cudaSuccess) return attr;
-    const size_t smem = (size_t)B * (L + L / 8 + 1) * sizeof(float2);
+    const size_t smem = (size_t)B * (line_pitch<L, Rs...>() + 1) * sizeof(float2);
     k_c2r_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
   }
   return cudaGetLastError();

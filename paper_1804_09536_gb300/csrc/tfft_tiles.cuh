@@ -81,9 +81,26 @@ __device__ __forceinline__ void line_sync() {
   }
 }
 
-// Padded position inside a contiguous line: one spare slot every 8 elements
-// keeps the stride-R Stockham writes free of shared-memory bank conflicts.
-__device__ __forceinline__ int cpad(int pos) { return pos + (pos >> 3); }
+// Padded position inside a contiguous line: one spare slot every P elements.
+// The first stage writes its outputs at stride R0 (its radix); with P = R0
+// that stride becomes R0 + 1, odd, so 16 lanes of 8-byte stores hit 16
+// distinct bank pairs.  P = 8 for a first radix below 8 or not a power of two.
+template <int... Rs>
+__host__ __device__ constexpr int pad_every() {
+  constexpr int r[] = {Rs...};
+  return (r[0] & (r[0] - 1)) == 0 && r[0] >= 8 ? r[0] : 8;
+}
+
+template <int P>
+__device__ __forceinline__ int padp(int pos) {
+  return pos + pos / P;
+}
+
+// Padded line pitch of the contiguous-line kernels (elements).
+template <int L, int... Rs>
+__host__ __device__ constexpr int line_pitch() {
+  return L + L / pad_every<Rs...>();
+}
 
 // ------------------------------------------------------------ contiguous lines
 
@@ -102,7 +119,8 @@ __device__ __forceinline__ float2 ld(const float2* p) {
 template <int L, int E, int B, bool CG, int... Rs>
 __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, float2* smem, int jt, int ly) {
   constexpr int T = L / E, NST = sizeof...(Rs);
-  constexpr int LP = L + L / 8;
+  constexpr int LP = line_pitch<L, Rs...>();
+  constexpr int P = pad_every<Rs...>();
   float2* sl = smem + ly * LP;
   const bool inv = a.sign > 0;
   const int64_t line = tile * B + ly;
@@ -130,12 +148,12 @@ __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, f
 #pragma unroll
       for (int q = 0; q < E / Rp; ++q)
 #pragma unroll
-        for (int r = 0; r < Rp; ++r) sl[cpad(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+        for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
       line_sync<T>();
 #pragma unroll
       for (int q = 0; q < E / R; ++q)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q * R + r] = sl[cpad(jt + q * T + r * (L / R))];
+        for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
     }
     spec_stage<L, E, R, Ns>(v, jt, a.tw);
   });

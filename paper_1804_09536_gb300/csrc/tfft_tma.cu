@@ -13,20 +13,17 @@
 // buffered three deep: the copy of tile i+1 runs while tile i is
 // transformed and the store of tile i-1 drains.
 //
-// Contiguous passes stream B whole lines per tile with 1-D bulk copies, also
-// double-buffered.
-//
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // TFFT_DEVICE_ETIMEOUT in the plan's status word and leaves.
 #include <cuda.h>
 
-#include <type_traits>
-
-#include "tfft_internal.h"
+#include "tfft_tiles.cuh"
 
 namespace tfft {
 
 namespace {
+
+using namespace tiles;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -101,14 +98,6 @@ __device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, const void*
       : "memory");
 }
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 template <int N>
@@ -117,54 +106,6 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-template <int S, int... Rs>
-__host__ __device__ constexpr int radix_at() {
-  constexpr int r[] = {Rs...};
-  return r[S];
-}
-
-template <int S, int... Rs>
-__host__ __device__ constexpr int span_at() {
-  constexpr int r[] = {Rs...};
-  int p = 1;
-  for (int i = 0; i < S; ++i) p *= r[i];
-  return p;
-}
-
-template <int I, int N, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(std::integral_constant<int, I>{});
-    static_for<I + 1, N>(f);
-  }
-}
-
-template <int L, int E, int R, int Ns>
-__device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2* __restrict__ tw) {
-  constexpr int T = L / E;
-#pragma unroll
-  for (int q = 0; q < E / R; ++q) {
-    if constexpr (Ns > 1) {
-      const int j = jt + q * T;
-      const int step = (j % Ns) * (L / (Ns * R));
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], __ldg(&tw[r * step]));
-    }
-    Dft<R>::run(&v[q * R]);
-  }
-}
-
-__device__ __forceinline__ int opaque_tid_x() {
-  int v;
-  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(v));
-  return v;
-}
-__device__ __forceinline__ int opaque_tid_y() {
-  int v;
-  asm volatile("mov.u32 %0, %%tid.y;" : "=r"(v));
-  return v;
-}
 
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls of the second, clean-up wait
 
@@ -188,6 +129,21 @@ __device__ __forceinline__ void tile_coords(const TmaGeo& G, int axis, int k, in
 }
 
 // ------------------------------------------------------------ strided, TMA
+
+// Outer index and column block of a tile.  The default order runs the column
+// blocks fastest; `outer_fastest` runs the outer index fastest, so the CTAs
+// that run at the same time share one column block across neighbouring
+// outer indices (measured faster for the axis-0 pass of a 3-D array).
+__device__ __forceinline__ void tile_place(const StridedArgs& a, int64_t tile, int64_t& o, int2& blk) {
+  if (a.outer_fastest) {
+    const int64_t cb = tile / a.nouter;
+    o = tile - cb * a.nouter;
+    blk = a.colblocks[cb];
+  } else {
+    o = tile / a.ncolblocks;
+    blk = a.colblocks[tile - o * a.ncolblocks];
+  }
+}
 
 // Shared memory of the strided TMA kernel: three L x (W + 1) tile buffers.
 __host__ __device__ constexpr size_t strided_tma_smem(int L, int W) {
@@ -220,8 +176,9 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
   __syncthreads();
 
   auto issue_load = [&](int64_t tile, float2* dst, uint64_t* bar) {
-    const int64_t o = tile / a.ncolblocks;
-    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+    int64_t o;
+    int2 blk;
+    tile_place(a, tile, o, blk);
     mbar_expect_tx(bar, tile_bytes);
     for (int k = 0; k < gin.nops; ++k) {
       int c[5];
@@ -299,8 +256,9 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
-      const int64_t o = tile / a.ncolblocks;
-      const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+      int64_t o;
+      int2 blk;
+      tile_place(a, tile, o, blk);
       for (int k = 0; k < gout.nops; ++k) {
         int c[5];
         tile_coords(gout, a.axis, k, blk.x, o, tax, c);
@@ -310,113 +268,6 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
     }
   }
   if (tid == 0) bulk_wait_all();
-}
-
-// ------------------------------------------------------------ contiguous, bulk copies
-
-template <int L, int E, int B, int... Rs>
-__global__ void __launch_bounds__((L / E) * B, 1)
-    k_contig_tma(const ContigArgs a) {
-  constexpr int T = L / E, NST = sizeof...(Rs);
-  constexpr int LP = L + L / 8;
-  extern __shared__ __align__(128) float2 smem[];
-  float2* in0 = smem;
-  float2* in1 = smem + B * L;
-  float2* xch = smem + 2 * B * L;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * B * L + B * LP);
-  const int ly = threadIdx.y;
-  const int tid = ly * T + threadIdx.x;
-  const bool inv = a.sign > 0;
-  const int64_t ntiles = (a.nlines + B - 1) / B;
-  float2* sl = xch + ly * LP;
-
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_mbar_init();
-    fence_proxy_async();
-  }
-  __syncthreads();
-  auto issue = [&](int64_t tile, float2* dst, uint64_t* bar) {
-    const int64_t first = tile * B;
-    const int64_t nl = (a.nlines - first < B) ? (a.nlines - first) : B;
-    const uint32_t bytes = (uint32_t)(nl * L * sizeof(float2));
-    mbar_expect_tx(bar, bytes);
-    bulk_load(dst, a.in + first * L, bytes, bar);
-  };
-  int64_t tile = blockIdx.x;
-  if (tid == 0 && tile < ntiles) issue(tile, in0, &bars[0]);
-  int it = 0;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
-    float2* cur = (it & 1) ? in1 : in0;
-    float2* nxt = (it & 1) ? in0 : in1;
-    const int64_t next = tile + gridDim.x;
-    if (tid == 0 && next < ntiles) {
-      fence_proxy_async();
-      issue(next, nxt, &bars[(it + 1) & 1]);
-    }
-    bool ok = true;
-    if (!mbar_wait(&bars[it & 1], (it >> 1) & 1, a.wait_limit)) ok = false;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
-        mbar_wait(&bars[it & 1], (it >> 1) & 1, kWaitLimit);
-        if (next < ntiles) mbar_wait(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kWaitLimit);
-      }
-      break;
-    }
-    const int64_t line = tile * B + ly;
-    const bool act = line < a.nlines;
-    const int jt = opaque_tid_x();
-    const float2* src = cur + ly * L;
-    float2* dst = a.out + line * L;
-    float2 v[E];
-    static_for<0, NST>([&](auto S) {
-      constexpr int s = decltype(S)::value;
-      constexpr int R = radix_at<s, Rs...>();
-      constexpr int Ns = span_at<s, Rs...>();
-      if constexpr (s == 0) {
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            float2 x = src[jt + q * T + r * (L / R)];
-            if (inv) x.y = -x.y;
-            v[q * R + r] = x;
-          }
-      } else {
-        constexpr int Rp = radix_at<s - 1, Rs...>();
-        constexpr int Nsp = Ns / Rp;
-        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
-#pragma unroll
-        for (int q = 0; q < E / Rp; ++q)
-#pragma unroll
-          for (int r = 0; r < Rp; ++r) {
-            const int pos = stockham_out_index(jt + q * T, Nsp, Rp, r);
-            sl[pos + (pos >> 3)] = v[q * Rp + r];
-          }
-        if constexpr (T <= 32) __syncwarp(); else __syncthreads();
-#pragma unroll
-        for (int q = 0; q < E / R; ++q)
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int pos = jt + q * T + r * (L / R);
-            v[q * R + r] = sl[pos + (pos >> 3)];
-          }
-      }
-      spec_stage<L, E, R, Ns>(v, jt, a.tw);
-    });
-    constexpr int RL = radix_at<NST - 1, Rs...>();
-#pragma unroll
-    for (int q = 0; q < E / RL; ++q)
-#pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        float2 x = cscale(v[q * RL + r], a.scale);
-        if (inv) x.y = -x.y;
-        if (act) dst[jt + q * T + r * (L / RL)] = x;
-      }
-    __syncthreads();  // every thread is done with `cur` before it is refilled
-  }
 }
 
 template <class K>
@@ -460,21 +311,6 @@ cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo
   return cudaGetLastError();
 }
 
-template <int L, int E, int B, int... Rs>
-cudaError_t run_contig_tma(const ContigArgs& a, cudaStream_t s) {
-  auto kern = k_contig_tma<L, E, B, Rs...>;
-  static cudaError_t attr = allow_smem(kern);
-  if (attr != cudaSuccess) return attr;
-  const size_t smem = (2 * (size_t)B * L + (size_t)B * (L + L / 8)) * sizeof(float2) + 2 * sizeof(uint64_t);
-  const int threads = (L / E) * B;
-  static const int64_t slots = persistent_grid(kern, threads, smem, int64_t(1) << 40);
-  const int64_t ntiles = (a.nlines + B - 1) / B;
-  const int64_t grid = ntiles < slots ? ntiles : slots;
-  if (grid < 1) return cudaSuccess;
-  kern<<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
-  return cudaGetLastError();
-}
-
 // Strided TMA variants: length, elements per thread, tile width, radices.
 // The first row of a length is its default; tma_strided_variant() can pick
 // another (autotuning).
@@ -484,13 +320,6 @@ cudaError_t run_contig_tma(const ContigArgs& a, cudaStream_t s) {
   X(256, 16, 32, 16, 16)        \
   X(512, 32, 16, 32, 16)        \
   X(512, 16, 16, 8, 8, 8)
-
-// Contiguous TMA variants: length, elements per thread, lines per tile, radices.
-#define TFFT_TMA_CONTIG(X)      \
-  X(64, 8, 32, 8, 8)            \
-  X(128, 16, 16, 16, 8)         \
-  X(256, 16, 8, 16, 16)         \
-  X(512, 32, 16, 32, 16)
 
 }  // namespace
 
@@ -511,20 +340,6 @@ bool tma_strided_variant(int L, int want_W, int want_E, int& E, int& W) {
   return found;
 }
 
-bool tma_contig_plan(int L, int& E, int& B) {
-  switch (L) {
-#define X(LL, EE, BB, ...) \
-  case LL:                 \
-    E = EE;                \
-    B = BB;                \
-    return true;
-    TFFT_TMA_CONTIG(X)
-#undef X
-    default:
-      return false;
-  }
-}
-
 cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gi, const TmaGeo& go,
                                const void* tmap_in, const void* tmap_out, cudaStream_t s) {
   const CUtensorMap& ti = *static_cast<const CUtensorMap*>(tmap_in);
@@ -535,18 +350,6 @@ cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gi, co
   TFFT_TMA_STRIDED(X)
 #undef X
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_contig_tma(const ContigArgs& a, cudaStream_t s) {
-  switch (a.ap.L) {
-#define X(LL, EE, BB, ...) \
-  case LL:                 \
-    return run_contig_tma<LL, EE, BB, __VA_ARGS__>(a, s);
-    TFFT_TMA_CONTIG(X)
-#undef X
-    default:
-      return cudaErrorInvalidValue;
-  }
 }
 
 }  // namespace tfft
