@@ -80,8 +80,15 @@ TFFT_HD int64_t layout_addr(const DevLayout& L, int64_t g0, int64_t g1, int64_t 
 
 TFFT_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 TFFT_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The rounding order is spelled out on the device, so every kernel that
+// applies the same twiddle gets the same bits, however the compiler would
+// otherwise contract the products into FMAs.
 TFFT_HD float2 cmul(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+#else
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+#endif
 }
 TFFT_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // multiply by -i (the forward quarter turn)

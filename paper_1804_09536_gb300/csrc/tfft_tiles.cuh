@@ -49,6 +49,55 @@ __device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2*
   }
 }
 
+// Twiddles of every stage after the first for one thread, held in registers.
+// They depend only on the thread's position in the line, so a persistent
+// kernel loads them once instead of once per tile.  Stage s (span Ns, radix
+// R) multiplies item r of butterfly q by w_L^{r (j % Ns) L / (Ns R)} with
+// j = jt + q T; the values are stored from offset(s) on, (R - 1) per q.
+template <int L, int E, int... Rs>
+struct StageTwiddles {
+  static constexpr int NST = sizeof...(Rs);
+  __host__ __device__ static constexpr int offset(int s) {
+    constexpr int r[] = {Rs...};
+    int c = 0;
+    for (int i = 1; i < s; ++i) c += (E / r[i]) * (r[i] - 1);
+    return c;
+  }
+  static constexpr int COUNT = offset(NST);
+  float2 w[COUNT > 0 ? COUNT : 1];
+
+  __device__ __forceinline__ void load(int jt, const float2* __restrict__ tw) {
+    constexpr int T = L / E;
+    static_for<1, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      constexpr int off = offset(s);
+#pragma unroll
+      for (int q = 0; q < E / R; ++q) {
+        const int step = ((jt + q * T) % Ns) * (L / (Ns * R));
+#pragma unroll
+        for (int r = 1; r < R; ++r) w[off + q * (R - 1) + r - 1] = __ldg(&tw[r * step]);
+      }
+    });
+  }
+
+  // Stage s on a thread's items with the held twiddles.
+  template <int s>
+  __device__ __forceinline__ void stage(float2 (&v)[E]) const {
+    constexpr int R = radix_at<s, Rs...>();
+    constexpr int off = offset(s);
+#pragma unroll
+    for (int q = 0; q < E / R; ++q) {
+      if constexpr (s > 0) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], w[off + q * (R - 1) + r - 1]);
+      }
+      Dft<R>::run(&v[q * R]);
+    }
+  }
+};
+
 // threadIdx re-read inside a loop body, opaque to the compiler: it keeps the
 // per-thread shared-memory addresses from being hoisted out of the tile loop
 // (and held in registers across it).

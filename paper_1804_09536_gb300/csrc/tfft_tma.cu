@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
 
   int64_t tile = blockIdx.x;
   if (tid == 0 && tile < ntiles) issue_load(tile, smem, &bars[0]);
+  StageTwiddles<L, E, Rs...> twr;
+  twr.load(threadIdx.y, a.tw);
   int it = 0, b = 0;  // b = it % 3
   for (; tile < ntiles; tile += gridDim.x, ++it, b = (b == 2) ? 0 : b + 1) {
     float2* cur = smem + b * BUF;
@@ -241,7 +243,7 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
 #pragma unroll
           for (int r = 0; r < R; ++r) v[q * R + r] = cur[(jt + q * T + r * (L / R)) * WP + cx];
       }
-      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+      twr.template stage<s>(v);
     });
     constexpr int RL = radix_at<NST - 1, Rs...>();
     __syncthreads();
