@@ -259,10 +259,11 @@ int tfft_plan_set_launch_events(tfft_plan plan, void *const *events, int count);
  * Batched persistent executor: the fused transforms (one direction) of many
  * independent complex-to-complex plans -- each with its own shape and
  * virtual grid -- run by ONE kernel launch.  The launch's CTAs take the tiles
- * of every pass of every transform from a shared queue in pass order; a tile
- * of pass k of a transform waits (bounded, ~2 s, then the device status word
- * gets TFFT_DEVICE_ETIMEOUT = 1 and the launch stops) until every tile of pass
- * k-1 of the same transform is done.
+ * of every pass of every transform from a shared queue, segment by segment
+ * (segment = one pass of one transform) in pass-major order.  A tile of
+ * pass k of a transform waits (bounded,
+ * ~2 s, then the device status word gets TFFT_DEVICE_ETIMEOUT = 1 and the
+ * launch stops) until every tile of pass k-1 of the same transform is done.
  *
  *   tfft_batch_create   plans (host objects, bound before tfft_batch_bind)
  *   tfft_batch_state_bytes / tfft_batch_bind
@@ -291,6 +292,9 @@ int tfft_batch_execute(tfft_batch batch, void *stream);
 int tfft_batch_autotune(tfft_batch batch, int reps, void *stream);
 /* Work items (tiles) and segments (transform passes) of one execute. */
 int tfft_batch_num_items(tfft_batch batch, int64_t *items, int *segments);
+/* Issue order: segment `index` (0 <= index < segments) is pass `pass` of
+   transform `transform` (index into the create call's plans).  Host only. */
+int tfft_batch_segment(tfft_batch batch, int index, int *transform, int *pass);
 /* Executor tile variant chosen for passes of `kind` (0 contiguous, 1 strided) and length L. */
 int tfft_batch_variant(tfft_batch batch, int kind, int L, int *variant);
 /* Clock cycles a batch tile may wait for the previous pass (0: default ~2 s);

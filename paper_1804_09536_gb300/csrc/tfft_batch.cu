@@ -51,8 +51,12 @@ __device__ __forceinline__ void run_tile(const BatchSeg& S, int64_t tile, float2
 // Segments whose first-item table fits shared memory use it for the lookup.
 constexpr int kSmemSegs = 1024;
 
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const BatchArgs b) {
+__global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const BatchArgs b) {
   extern __shared__ float2 smem[];
+  // the current item's segment, copied out of global memory: read there, its
+  // fields would be reloaded after every global store of a tile (the
+  // compiler cannot rule out that the store changed them)
+  __shared__ __align__(16) BatchSeg s_S;
   __shared__ long long s_first[kSmemSegs];
   __shared__ long long s_item;
   __shared__ int s_seg;
@@ -64,6 +68,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const BatchArgs b) {
   // items are taken one ahead: the next one is claimed while the current one runs
   long long next = 0;
   if (tid == 0) next = (long long)atomicAdd(b.head, 1ull);
+  int cur_seg = -1;
   __syncthreads();
   for (;;) {
     if (tid == 0) {
@@ -107,7 +112,15 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch(const BatchArgs b) {
     const long long item = s_item;
     const int seg = s_seg;
     if (item >= b.nitems || s_abort) break;
-    const BatchSeg& S = b.segs[seg];
+    if (seg != cur_seg) {
+      static_assert(sizeof(BatchSeg) % sizeof(int) == 0, "segment copied as words");
+      const int* src = reinterpret_cast<const int*>(&b.segs[seg]);
+      int* dst = reinterpret_cast<int*>(&s_S);
+      for (int i = tid; i < (int)(sizeof(BatchSeg) / sizeof(int)); i += kBatchThreads) dst[i] = src[i];
+      cur_seg = seg;
+      __syncthreads();
+    }
+    const BatchSeg& S = s_S;
     // an item is a run of up to `per_item` consecutive tiles of one segment
     const int64_t t0 = (item - S.first) * S.per_item;
     const int64_t t1 = (t0 + S.per_item < S.ntiles) ? t0 + S.per_item : S.ntiles;

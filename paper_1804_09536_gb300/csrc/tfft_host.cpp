@@ -1354,13 +1354,29 @@ struct BatchSegH {
   size_t cb_cap;  // column-block slots reserved (strided)
 };
 
+// Issue order of the (transform, pass) segments: pass-major (every
+// transform's first pass, then every second pass, ...).  Items are taken in
+// this order, so a pass's producer was queued a whole round of passes
+// earlier and its waits are rare.  Orders that queue a transform's next pass
+// sooner, for L2 reuse, measured slower on the 48-transform workload: the
+// waits cost more than the reuse saves.
+std::vector<std::pair<int, int>> batch_order(const std::vector<std::vector<Step>>& steps) {
+  size_t maxpass = 0;
+  for (const auto& v : steps) maxpass = std::max(maxpass, v.size());
+  std::vector<std::pair<int, int>> order;
+  for (size_t pass = 0; pass < maxpass; ++pass)
+    for (size_t t = 0; t < steps.size(); ++t)
+      if (pass < steps[t].size()) order.emplace_back((int)t, (int)pass);
+  return order;
+}
+
 }  // namespace
 
 struct tfft_batch_s {
   int sign = TFFT_FORWARD;
   std::vector<tfft_plan> plans;
   std::vector<std::vector<Step>> steps;       // per transform, fused, buffers assigned at bind
-  std::vector<BatchSegH> segs;                // pass-major
+  std::vector<BatchSegH> segs;                // in issue order (batch_order)
   std::map<std::pair<int, int>, int> choice;  // (kind, L) -> executor variant
   std::vector<void*> ins, outs, works;
   char* d_state = nullptr;
@@ -1501,7 +1517,6 @@ int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int si
   if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
   auto b = new tfft_batch_s();
   b->sign = sign;
-  int maxpass = 0;
   for (int t = 0; t < count; ++t) {
     tfft_plan p = plans[t];
     if (!p || !p->transformable || p->kind != TFFT_C2C || p->nelems >= (int64_t(1) << 31)) {
@@ -1518,34 +1533,33 @@ int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int si
       }
       if (!b->choice.count({kind, s.L})) b->choice[{kind, s.L}] = batch_candidates(kind, s.L)[0];
     }
-    maxpass = std::max(maxpass, (int)b->steps.back().size());
   }
-  // segments, pass-major; column-block capacity for the narrowest candidate
+  // segments in issue order (see batch_order); column-block capacity for the
+  // narrowest candidate
   std::vector<std::vector<int>> idx(count);
   size_t cb_total = 0;
-  for (int pass = 0; pass < maxpass; ++pass)
-    for (int t = 0; t < count; ++t) {
-      if (pass >= (int)b->steps[t].size()) continue;
-      const Step& s = b->steps[t][pass];
-      BatchSegH h;
-      h.t = t;
-      h.pass = pass;
-      h.kind = s.kind == S_CONTIG ? 0 : 1;
-      h.L = s.L;
-      h.prev = pass > 0 ? idx[t][pass - 1] : -1;
-      h.ntiles = 0;
-      h.cb_cap = 0;
-      if (h.kind == 1)
-        for (int v : batch_candidates(1, s.L)) {
-          int k, l, e, bw;
-          AxisPlan ap;
-          batch_variant(v, k, l, e, bw, ap);
-          h.cb_cap = std::max(h.cb_cap, colblock_list(b->plans[t], s.lin, s.lout, bw).size());
-        }
-      cb_total += align_up(h.cb_cap * sizeof(int2), 256);
-      idx[t].push_back((int)b->segs.size());
-      b->segs.push_back(h);
-    }
+  for (const auto& tp : batch_order(b->steps)) {
+    const int t = tp.first, pass = tp.second;
+    const Step& s = b->steps[t][pass];
+    BatchSegH h;
+    h.t = t;
+    h.pass = pass;
+    h.kind = s.kind == S_CONTIG ? 0 : 1;
+    h.L = s.L;
+    h.prev = pass > 0 ? idx[t][pass - 1] : -1;
+    h.ntiles = 0;
+    h.cb_cap = 0;
+    if (h.kind == 1)
+      for (int v : batch_candidates(1, s.L)) {
+        int k, l, e, bw;
+        AxisPlan ap;
+        batch_variant(v, k, l, e, bw, ap);
+        h.cb_cap = std::max(h.cb_cap, colblock_list(b->plans[t], s.lin, s.lout, bw).size());
+      }
+    cb_total += align_up(h.cb_cap * sizeof(int2), 256);
+    idx[t].push_back((int)b->segs.size());
+    b->segs.push_back(h);
+  }
   b->ctr_off = 256;
   b->seg_off = b->ctr_off + align_up(16 + b->segs.size() * sizeof(int), 256);
   b->cb_off = b->seg_off + align_up(b->segs.size() * sizeof(BatchSeg), 256);
@@ -1554,6 +1568,14 @@ int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int si
   b->outs.assign(count, nullptr);
   b->works.assign(count, nullptr);
   *out = b;
+  return TFFT_OK;
+}
+
+int tfft_batch_segment(tfft_batch b, int index, int* transform, int* pass) {
+  if (!b || !transform || !pass) return fail(TFFT_EINVAL, "NULL argument");
+  if (index < 0 || index >= (int)b->segs.size()) return fail(TFFT_EINVAL, "segment index out of range");
+  *transform = b->segs[index].t;
+  *pass = b->segs[index].pass;
   return TFFT_OK;
 }
 

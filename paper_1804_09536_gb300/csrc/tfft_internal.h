@@ -114,7 +114,7 @@ cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
 
 // Batched persistent executor (tfft_batch.cu).  One segment = the tiles of
 // one pass of one transform; items are numbered consecutively over the
-// segments (pass-major order).
+// segments, pass-major.
 struct BatchSeg {
   int kind;         // 0 contiguous, 1 strided
   int variant;      // executor tile variant

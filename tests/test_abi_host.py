@@ -108,3 +108,39 @@ def test_launch_counts(lib):
     assert p.num_launches(-1, "unfused") == 5
     # packed: the 2 -> 1 exchange needs pack + all-to-all + unpack, 1 -> 0 needs pack + all-to-all
     assert p.num_launches(-1, "packed") >= 7
+
+
+def _batch_order(lib, problems):
+    from paper_1804_09536_gb300.plan import Plan
+    plans = [Plan(sh, gr, bind=False) for sh, gr in problems]
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    b = ctypes.c_void_p()
+    assert lib.tfft_batch_create(ctypes.byref(b), len(plans), arr, -1) == 0
+    try:
+        items, segs = ctypes.c_int64(), ctypes.c_int()
+        assert lib.tfft_batch_num_items(b, ctypes.byref(items), ctypes.byref(segs)) == 0
+        t, k = ctypes.c_int(), ctypes.c_int()
+        order = []
+        for i in range(segs.value):
+            assert lib.tfft_batch_segment(b, i, ctypes.byref(t), ctypes.byref(k)) == 0
+            order.append((t.value, k.value))
+        assert lib.tfft_batch_segment(b, segs.value, ctypes.byref(t), ctypes.byref(k)) == 1
+        npass = [p.num_launches(-1, "fused") for p in plans]
+    finally:
+        lib.tfft_batch_destroy(b)
+    return order, npass
+
+
+@pytest.mark.parametrize("which", ["bench48", "mixed"])
+def test_batch_issue_order(lib, which):
+    """Every pass of every transform exactly once, pass-major: all first
+    passes (transform order), then all second passes, ..."""
+    from paper_1804_09536_gb300 import inputs
+    if which == "bench48":
+        problems = inputs.batch_problems(48, seed=0)
+    else:
+        problems = [((256, 256, 256), (2, 4)), ((64, 96), (4,)), ((128, 128, 128), (2, 2)),
+                    ((128,), ()), ((96, 96, 96), (2, 2))]
+    order, npass = _batch_order(lib, problems)
+    want = [(t, k) for k in range(max(npass)) for t in range(len(problems)) if k < npass[t]]
+    assert order == want
