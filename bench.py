@@ -259,6 +259,10 @@ def run_ours(args):
     r2c = r2c_slab(plan_cls=Plan, dev=dev, steps=max(5, min(args.steps, 50)), barrier=barrier,
                    tma=not args.no_tma)
 
+    # the 4-D case: 128^4 on a 3-D virtual grid
+    fd = fourd_128(plan_cls=Plan, dev=dev, steps=max(3, min(args.steps, 20)), barrier=barrier,
+                   tma=not args.no_tma)
+
     # the tensor-core radix-16 stage on the same workload, FP32 beside it
     tc = tc_modes(x, y, dev, steps=max(3, min(args.steps, 20)), barrier=barrier, ms_fp32=ms_step)
     # the differentiable 512^3 workload: loss = sum |F(x) w|^2 and its gradient
@@ -329,6 +333,7 @@ def run_ours(args):
                                    "packed": round(extra["packed"], 4)},
         "fused_vs_packed_speedup": round(extra["packed"] / ms_step, 3),
         "r2c_slab_256": r2c,
+        "fourd_128": fd,
         "tensor_core_512": tc,
         "autograd_512": ag,
         "batch48": bt,
@@ -390,6 +395,51 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True):
             "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
             "note": "c2r overwrites its input; the forward output is reused as the inverse's input"}
+
+
+def fourd_128(plan_cls, dev, steps, barrier, tma=True):
+    """128^4 c2c on a virtual 4 x 4 x 2 grid (a 4-D array on a 3-D grid, the
+    paper's 4-D case): forward + inverse, fused and packed; ms per step and
+    the HBM fraction of the fused path's algorithmic bytes."""
+    import torch
+    from paper_1804_09536_gb300 import inputs
+    shape, grid = (128, 128, 128, 128), (4, 4, 2)
+    p = plan_cls(shape, grid, device=dev, tma=tma)
+    x = p.scatter(inputs.normal_complex(shape, seed=0).to(dev), 0)
+    y = p.empty_stage(p.g)
+    z = p.empty_stage(0)
+    out = {}
+    nbytes = 0
+    for mode in ("fused", "packed"):
+        w = p.workspace(mode)
+
+        def one():
+            p.execute(-1, x, y, mode, w)
+            p.execute(+1, y, z, mode, w)
+        for _ in range(2):
+            one()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            one()
+        b.record()
+        barrier()
+        out[mode] = a.elapsed_time(b) / steps
+        if mode == "fused":
+            nbytes = sum(n for _, n in p.launch_info(-1, mode) + p.launch_info(+1, mode))
+            err = float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x))
+        del w
+    peak, _ = _peaks()
+    n = math.prod(shape)
+    return {"workload": "128x128x128x128 c2c complex64, virtual grid 4x4x2, forward+inverse",
+            "fused_ms": round(out["fused"], 4), "packed_ms": round(out["packed"], 4),
+            "fused_vs_packed_speedup": round(out["packed"] / out["fused"], 3),
+            "GFLOPs": round(2 * 5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
+            "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
+            "kernels": sorted({k for k, _ in p.launch_info(-1, "fused")}),
+            "round_trip_rel_l2": err}
 
 
 def tc_modes(x, y_fp32, dev, steps, barrier, ms_fp32):

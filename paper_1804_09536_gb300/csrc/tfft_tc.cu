@@ -176,9 +176,11 @@ constexpr int kRows = kLines * 32;                 // 256 sub-transforms per til
 constexpr uint32_t kOpBytes = (kRows / 8) * kSBO;  // one 256 x 32 16-bit operand
 constexpr uint32_t kBBytes = (32 / 8) * kSBO;      // the 32 x 32 DFT operand
 constexpr uint32_t kTmemCols = 64;                 // two FP32 groups of 32 columns
+constexpr int kCtasPerSm = 4;                      // 4 x 64 of the 512 tensor-memory columns
+static_assert(kCtasPerSm * kTmemCols <= 512, "tensor memory columns per SM");
 
 template <int FMT>
-__global__ void __launch_bounds__(kThreads, 1) k_contig_tc512(const ContigArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const ContigArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   uint8_t* a_hi = sm;
   uint8_t* a_lo = sm + kOpBytes;
@@ -316,15 +318,13 @@ cudaError_t run_tc(const ContigArgs& a, cudaStream_t s) {
   static cudaError_t attr =
       cudaFuncSetAttribute(k_contig_tc512<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (attr != cudaSuccess) return attr;
+  // kCtasPerSm resident CTAs per SM (the launch bounds' promise); the grid
+  // is a persistent tile loop, so extra CTAs would only queue
   static const int slots = [] {
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_contig_tc512<FMT>, kThreads,
-                                                  2 * kOpBytes + 2 * kBBytes + 16);
-    if (per < 1) per = 1;
-    if (per > 512 / (int)kTmemCols) per = 512 / (int)kTmemCols;  // tensor memory columns per SM
-    return (sms > 0 ? sms : 1) * per;
+    return (sms > 0 ? sms : 1) * kCtasPerSm;
   }();
   const int64_t ntiles = (a.nlines + kLines - 1) / kLines;
   const int64_t grid = ntiles < slots ? ntiles : slots;

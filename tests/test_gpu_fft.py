@@ -26,6 +26,7 @@ CASES = [
     ((16, 32, 64), (4,)),            # slab
     ((5, 6, 8), (4, 3)),             # zero-size ranks on axis 0
     ((12, 10, 8, 6), (2, 3, 2)),     # 4-D on a 3-D grid
+    ((32, 32, 32, 32), (2, 2, 2)),   # 4-D, several tiles per pass
     ((64, 96), (4,)),                # 2-D slab
     ((128,), ()),                    # 1-D, no grid
     ((1, 16, 8), (1, 2)),            # length-1 axis
@@ -174,6 +175,33 @@ def test_full_size_512_pencil_sampled(cuda_device):
     rms = float(np.sqrt(np.mean(np.abs(yg.astype(np.complex128)) ** 2)))
     assert np.max(np.abs(got - want)) <= 1e-4 * rms
     # Parseval (paper normalisation) and round trip hold at any size
+    n = x.numel()
+    e_in = float(torch.sum(torch.abs(x.to(torch.complex128)) ** 2)) / n
+    e_out = float(np.sum(np.abs(yg.astype(np.complex128)) ** 2))
+    assert abs(e_out - e_in) <= 1e-5 * e_in
+    back = p.inverse(y)
+    diff = torch.linalg.vector_norm((back - b0).to(torch.complex128)) / torch.linalg.vector_norm(b0.to(torch.complex128))
+    assert float(diff) <= RTOL_FP32
+
+
+@pytest.mark.slow
+def test_full_size_128_4d_sampled(cuda_device):
+    """The 4-D workload of bench.py (128^4 on a 4 x 4 x 2 grid): sampled outputs
+    against the oracle's definition, Parseval and round trip."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (128, 128, 128, 128), (4, 4, 2)
+    x = inputs.normal_complex(shape, seed=0)
+    p = Plan(shape, grid, device=cuda_device)
+    b0 = p.scatter(x.to(cuda_device), 0)
+    y = p.forward(b0)
+    yg = p.gather(y, p.g).cpu().numpy()
+    rng = np.random.default_rng(1)
+    ks = [(0, 0, 0, 0), (127, 127, 127, 127), (1, 2, 3, 4)] + [
+        tuple(int(v) for v in rng.integers(0, 128, 4)) for _ in range(3)]
+    want = dft.forward_at(x.numpy(), ks, chunk=8)
+    got = np.array([yg[k] for k in ks])
+    rms = float(np.sqrt(np.mean(np.abs(yg.astype(np.complex128)) ** 2)))
+    assert np.max(np.abs(got - want)) <= 1e-4 * rms
     n = x.numel()
     e_in = float(torch.sum(torch.abs(x.to(torch.complex128)) ** 2)) / n
     e_out = float(np.sum(np.abs(yg.astype(np.complex128)) ** 2))
