@@ -513,9 +513,9 @@ def autograd_step(plan, x, dev, steps, barrier):
     barrier()
     ms = a.elapsed_time(b) / steps
     n = math.prod(SHAPE)
-    # algorithmic bytes: forward 3 sweeps (2 x 8 B), loss (read y 8 B + w 4 B), seed (read y, w,
-    # write z: 20 B), adjoint 3 sweeps
-    nbytes = n * (6 * 16 + 12 + 20)
+    # algorithmic bytes: forward 3 sweeps (2 x 8 B), the loss sweep (read y 8 B + w 4 B, write
+    # u = w^2 y 8 B), adjoint 3 sweeps (the factor 2 g applied by its last pass)
+    nbytes = n * (6 * 16 + 20)
     peak, _ = _peaks()
     return {"workload": "512^3 c2c pencil 4x8: loss = sum |F(x) w|^2, w U[0,1) seed 1; forward + loss "
                         "+ gradient (adjoint transform) via torch.autograd",

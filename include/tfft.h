@@ -195,20 +195,26 @@ int tfft_execute(tfft_plan plan, int sign, int mode, const void *in, void *out, 
  * runs the backward passes -- the forward's passes in reverse order, each
  * redistribution reversed (a permutation, whose adjoint is its inverse) --
  * with 1/N applied in the last pass (no factor under TFFT_NORM_BACKWARD).
- * Arguments as tfft_execute().
+ * d_coef (device memory, 8-byte aligned, may be NULL): the result is
+ * multiplied by d_coef[0], read on the device by the last pass, so a scalar
+ * known only on the GPU (an upstream gradient) costs no extra sweep and no
+ * host synchronisation.  Other arguments as tfft_execute().
  */
 int tfft_adjoint(tfft_plan plan, int mode, const void *in, void *out, void *work, size_t work_bytes,
-                 void *stream);
+                 const double *d_coef, void *stream);
 
 /*
  * Spectral-weight loss sum_k |y_k w_k|^2 over a whole stage buffer: y is
- * complex64, w is float32 in the same layout (w[i] weighs y[i]); the sum is
- * formed in double precision in a fixed order (deterministic) and written to
- * d_loss[0] (device memory).  Uses scratch inside the plan state: calls on one
- * plan must not overlap on the GPU.
+ * complex64, w is float32 in the same layout (w[i] weighs y[i]); each term and
+ * each thread's running sum are carried in compensated FP32 (about 48 bits),
+ * the rest in double, in a fixed order (deterministic); the sum is written to
+ * d_loss[0] (device memory).  When u is not NULL the same sweep writes
+ * u = w^2 y (complex64, same layout; u may alias y): the gradient of
+ * g * loss(F x) is then tfft_adjoint(u) with d_coef = 2 g.  Uses scratch
+ * inside the plan state: calls on one plan must not overlap on the GPU.
  */
 int tfft_weighted_energy(tfft_plan plan, int stage, const void *y, const float *w, double *d_loss,
-                         void *stream);
+                         void *u, void *stream);
 
 /*
  * Gradient seed of that loss: z = c * w^2 * y elementwise, c = scale * d_coef[0]

@@ -55,8 +55,8 @@ SIGNATURES = {
     "tfft_execute": [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp],
     "tfft_plan_num_launches": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "tfft_plan_set_launch_events": [_vp, ctypes.POINTER(_vp), ctypes.c_int],
-    "tfft_adjoint": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp],
-    "tfft_weighted_energy": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp],
+    "tfft_adjoint": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp, _vp],
+    "tfft_weighted_energy": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
     "tfft_weight_scale": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp],
     "tfft_batch_create": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int],
     "tfft_batch_destroy": [_vp],

@@ -2,11 +2,12 @@
 
 loss(x) = sum_k |F(x)_k w_k|^2, F the plan's forward transform (stage 0 ->
 stage g, paper normalisation).  Backward: d loss / d x = 2 F^H (w^2 F x)
-(d/dRe + i d/dIm convention used by torch for complex inputs), computed as
-the gradient seed z = 2 g w^2 y followed by the adjoint transform
-(tfft_adjoint: the backward passes with the redistributions reversed and
-1/N).  Every step runs in the library's kernels; the forward output y is
-kept for the backward.
+(d/dRe + i d/dIm convention used by torch for complex inputs).  The forward
+sweep that sums the loss also writes u = w^2 y over y (one pass over y and w);
+the backward is the adjoint transform of u (tfft_adjoint: the backward passes
+with the redistributions reversed and 1/N) with the factor 2 g applied on the
+device by its last pass, so the gradient seed is never materialised.  Every
+step runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -16,19 +17,18 @@ import torch
 class SpectralWeightLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x: torch.Tensor, w: torch.Tensor, plan) -> torch.Tensor:
-        y = plan.forward(x)                        # keeps x (workspace)
-        loss = plan.weighted_energy(plan.g, y, w)  # float64, deterministic
-        ctx.save_for_backward(y, w)
+        y = plan.forward(x)                             # keeps x (workspace)
+        loss = plan.weighted_energy(plan.g, y, w, u=y)  # float64, deterministic; y <- w^2 y
+        ctx.save_for_backward(y)
         ctx.plan = plan
         return loss
 
     @staticmethod
     def backward(ctx, gout: torch.Tensor):
-        y, w = ctx.saved_tensors
+        (u,) = ctx.saved_tensors
         plan = ctx.plan
-        g = gout.detach().to(torch.float64).reshape(()).contiguous()
-        z = plan.weight_scale(plan.g, y, w, g, 2.0)   # 2 g w^2 y
-        gx = plan.adjoint(z)
+        c = (2.0 * gout.detach().to(torch.float64)).reshape(()).contiguous()
+        gx = plan.adjoint(u, coef=c)  # 2 g F^H (w^2 y); u kept (a retained graph may run it again)
         return gx, None, None
 
 

@@ -67,6 +67,7 @@ struct Step {
   int sign = -1;
   bool scaled = false;
   double scale_value = 1.0;
+  const double* coef = nullptr;  // device factor on a contiguous pass's output (one call only)
   // box copies
   size_t box_off = 0;
   int nboxes = 0;
@@ -746,6 +747,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.lines_per_cta = a.ap.spec ? a.ap.width : std::max(1, 256 / a.ap.T);
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
+    a.coef = s.coef;
     a.status = reinterpret_cast<int*>(p->d_state);
     a.wait_limit = p->wait_limit;
     if (p->precision != TFFT_FP32 && tc_supported(a.ap.L))
@@ -1235,7 +1237,7 @@ int tfft_plan_set_launch_events(tfft_plan p, void* const* events, int count) {
 }
 
 static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
-                        size_t work_bytes, void* stream);
+                        size_t work_bytes, void* stream, const double* coef = nullptr);
 
 int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, void* work,
                  size_t work_bytes, void* stream) {
@@ -1243,12 +1245,14 @@ int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, voi
 }
 
 int tfft_adjoint(tfft_plan p, int mode, const void* in, void* out, void* work, size_t work_bytes,
-                 void* stream) {
+                 const double* d_coef, void* stream) {
   if (p && p->kind != TFFT_C2C) return fail(TFFT_EUNSUPPORTED, "the adjoint is built for complex-to-complex plans");
-  return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, in, out, work, work_bytes, stream);
+  if (d_coef && (reinterpret_cast<uintptr_t>(d_coef) & 7)) return fail(TFFT_EINVAL, "d_coef is misaligned");
+  return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, in, out, work, work_bytes, stream, d_coef);
 }
 
-int tfft_weighted_energy(tfft_plan p, int stage, const void* y, const float* w, double* d_loss, void* stream) {
+int tfft_weighted_energy(tfft_plan p, int stage, const void* y, const float* w, double* d_loss, void* u,
+                         void* stream) {
   if (!p) return fail(TFFT_EINVAL, "plan is NULL");
   if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
   if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
@@ -1256,9 +1260,10 @@ int tfft_weighted_energy(tfft_plan p, int stage, const void* y, const float* w, 
   if (rc) return rc;
   if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
   if (!d_loss || (reinterpret_cast<uintptr_t>(d_loss) & 7)) return fail(TFFT_EINVAL, "d_loss is NULL or misaligned");
+  if (u && (rc = check_ptr(u, "u"))) return rc;
   cudaError_t e = launch_weighted_energy(static_cast<const float2*>(y), w, p->st[stage].total,
                                          reinterpret_cast<double*>(p->d_state + p->red_off), kReductionParts,
-                                         d_loss, static_cast<cudaStream_t>(stream));
+                                         d_loss, static_cast<float2*>(u), static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return TFFT_OK;
 }
@@ -1280,7 +1285,7 @@ int tfft_weight_scale(tfft_plan p, int stage, const void* y, const float* w, con
 }
 
 static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
-                        size_t work_bytes, void* stream) {
+                        size_t work_bytes, void* stream, const double* coef) {
   if (!p) return fail(TFFT_EINVAL, "plan is NULL");
   if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
   if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
@@ -1301,6 +1306,13 @@ static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in
     if (a < b + out_bytes && b < a + in_bytes) return fail(TFFT_EINVAL, "in and out overlap");
   }
   std::vector<Step> steps = p->steps[{key, mode}];
+  if (coef) {  // the device factor goes on the last transform pass
+    int k = (int)steps.size() - 1;
+    while (k >= 0 && steps[k].kind == S_BOX) --k;
+    if (k < 0 || steps[k].kind != S_CONTIG)
+      return fail(TFFT_EUNSUPPORTED, "a device coefficient needs a contiguous last pass");
+    steps[k].coef = coef;
+  }
   void* w0 = nullptr;
   void* w1 = nullptr;
   bool destroy = false;

@@ -24,9 +24,18 @@ struct ContigArgs {
   int lines_per_cta;
   int sign;
   float scale;
+  const double* coef;   // optional device factor on the output (NULL: none)
   int* status;       // device status word
   uint32_t wait_limit;  // polls of a bounded copy wait (TMA passes)
 };
+
+#ifdef __CUDACC__
+// Output factor of a contiguous pass: the host's scale, times the device
+// coefficient when there is one (formed in double, applied in float).
+__device__ __forceinline__ float contig_scale(const ContigArgs& a) {
+  return a.coef ? (float)((double)a.scale * __ldg(a.coef)) : a.scale;
+}
+#endif
 
 // Real-to-complex (dir -1) or complex-to-real (dir +1) along the innermost
 // axis: lines of N = 2 L reals <-> lines of L + 1 complex (Hermitian half),
@@ -153,7 +162,7 @@ cudaError_t launch_contig_tc(const ContigArgs& a, int precision, cudaStream_t s)
 // `nparts` doubles of plan-state scratch.
 constexpr int kReductionParts = 1024;
 cudaError_t launch_weighted_energy(const float2* y, const float* w, int64_t n, double* parts, int nparts,
-                                   double* out, cudaStream_t s);
+                                   double* out, float2* u, cudaStream_t s);
 cudaError_t launch_weight_scale(const float2* y, const float* w, const double* coef, double scale, int64_t n,
                                 float2* z, cudaStream_t s);
 

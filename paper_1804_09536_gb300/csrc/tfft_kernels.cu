@@ -62,6 +62,7 @@ __device__ __forceinline__ int padpos(int pos) { return pos + (pos >> 4); }
 
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_fft_contig(const ContigArgs a) {
+  const float oscale = contig_scale(a);
   extern __shared__ float2 smem[];
   const int L = a.ap.L, T = a.ap.T, nst = a.ap.nst;
   const int jt = threadIdx.x, ly = threadIdx.y, B = blockDim.y;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(512, 2) k_fft_contig(const ContigArgs a) {
     const float2* src = a.in + line * L;
     float2* dst = a.out + line * L;
     if (nst == 0) {  // length-1 axis: the DFT is the identity
-      if (act && jt == 0) dst[0] = cscale(src[0], a.scale);
+      if (act && jt == 0) dst[0] = cscale(src[0], oscale);
       continue;
     }
     float2 v[E];
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(512, 2) k_fft_contig(const ContigArgs a) {
       for (int q = 0; q < E / RR; ++q)
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
-          float2 x = cscale(v[q * RR + r], a.scale);
+          float2 x = cscale(v[q * RR + r], oscale);
           if (inv) x.y = -x.y;
           if (act) dst[jt + q * T + r * (L / RR)] = x;
         }
@@ -285,6 +286,7 @@ __device__ __forceinline__ float2* generic_fft(float2* b0, float2* b1, const Axi
 }
 
 __global__ void __launch_bounds__(512) k_fft_contig_generic(const ContigArgs a) {
+  const float oscale = contig_scale(a);
   extern __shared__ float2 smem[];
   const int L = a.ap.L, T = a.ap.T;
   const int jt = threadIdx.x, ly = threadIdx.y, B = blockDim.y;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(512) k_fft_contig_generic(const ContigArgs a) 
     __syncthreads();
     const float2* res = generic_fft(b0, b1, a.ap, jt, 1, 0, a.tw);
     for (int i = jt; i < L; i += T) {
-      float2 x = cscale(res[i], a.scale);
+      float2 x = cscale(res[i], oscale);
       if (inv) x.y = -x.y;
       if (act) a.out[line * L + i] = x;
     }

@@ -44,14 +44,23 @@ __device__ __forceinline__ void weighted_term(float2 v, float w, float& hi, floa
   lo = __fmaf_rn(s, eq, __fmaf_rn(sl, q, et));
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_weighted_energy_part(const float2* __restrict__ y,
-                                                                      const float* __restrict__ w, int64_t n,
-                                                                      double* __restrict__ part) {
+// With U = true the same sweep also writes u = w^2 y (the gradient seed up to
+// its scalar factor), which may alias y.
+template <bool U>
+__global__ void __launch_bounds__(kRedThreads) k_weighted_energy_part(const float2* y, const float* __restrict__ w,
+                                                                      int64_t n, double* __restrict__ part,
+                                                                      float2* u) {
   __shared__ double red[kRedThreads];
   float ah = 0.f, al = 0.f;  // running sum, renormalised after every term
   for (int64_t i = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kRedThreads) {
     float th, tl, s, e;
-    weighted_term(y[i], w[i], th, tl);
+    const float2 v = y[i];
+    const float wi = w[i];
+    weighted_term(v, wi, th, tl);
+    if constexpr (U) {
+      const float f = wi * wi;
+      u[i] = make_float2(f * v.x, f * v.y);
+    }
     two_sum(ah, th, s, e);
     const float l = __fadd_rn(__fadd_rn(al, e), tl);
     ah = __fadd_rn(s, l);  // fast two-sum: |s| >= |l|
@@ -93,8 +102,11 @@ __global__ void k_weight_scale(const float2* __restrict__ y, const float* __rest
 }  // namespace
 
 cudaError_t launch_weighted_energy(const float2* y, const float* w, int64_t n, double* parts, int nparts,
-                                   double* out, cudaStream_t s) {
-  k_weighted_energy_part<<<nparts, kRedThreads, 0, s>>>(y, w, n, parts);
+                                   double* out, float2* u, cudaStream_t s) {
+  if (u)
+    k_weighted_energy_part<true><<<nparts, kRedThreads, 0, s>>>(y, w, n, parts, u);
+  else
+    k_weighted_energy_part<false><<<nparts, kRedThreads, 0, s>>>(y, w, n, parts, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_sum_parts<<<1, kRedThreads, 0, s>>>(parts, nparts, out);

@@ -118,11 +118,24 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     const float2* src = a.cin + line * (L + 1);
     float2* dst = reinterpret_cast<float2*>(a.rout) + line * L;
     const int jt = opaque_tid_x();
+    // the L + 1 inputs: every load issued before the first shared store, so
+    // that they are all in flight together
+    constexpr int NK = E + 1;  // ceil((L + 1) / T)
+    float2 xin[NK];
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+      const int k = jt + i * T;
+      xin[i] = (act && k <= L) ? src[k] : make_float2(0.f, 0.f);
+    }
     line_sync<T>();  // the previous line group is done with sl
-    for (int k = jt; k <= L; k += T) {
-      float2 x = act ? src[k] : make_float2(0.f, 0.f);
-      if (k == 0 || k == L) x.y = 0.f;
-      sl[padp<P>(k)] = x;
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+      const int k = jt + i * T;
+      if (k <= L) {
+        float2 x = xin[i];
+        if (k == 0 || k == L) x.y = 0.f;
+        sl[padp<P>(k)] = x;
+      }
     }
     line_sync<T>();
     float2 v[E];

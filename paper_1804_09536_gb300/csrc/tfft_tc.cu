@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   constexpr uint32_t idesc = instr_desc((uint32_t)FMT, 128, 32);
+  const float oscale = contig_scale(a);
   bool failed = false;
   uint32_t phase = 0;
 
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
         const int j = tid & 31;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          float2 y = make_float2(r[2 * k] * a.scale, r[2 * k + 1] * a.scale);
+          float2 y = make_float2(r[2 * k] * oscale, r[2 * k + 1] * oscale);
           if (inv) y.y = -y.y;
           dst[j + 32 * k] = y;
         }

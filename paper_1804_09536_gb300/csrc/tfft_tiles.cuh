@@ -207,11 +207,12 @@ __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, f
     spec_stage<L, E, R, Ns>(v, jt, a.tw);
   });
   constexpr int RL = radix_at<NST - 1, Rs...>();
+  const float oscale = contig_scale(a);
 #pragma unroll
   for (int q = 0; q < E / RL; ++q)
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
-      float2 x = cscale(v[q * RL + r], a.scale);
+      float2 x = cscale(v[q * RL + r], oscale);
       if (inv) x.y = -x.y;
       if (act) dst[jt + q * T + r * (L / RL)] = x;
     }

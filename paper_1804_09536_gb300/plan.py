@@ -165,22 +165,26 @@ class Plan:
         return self.execute(_lib.TFFT_BACKWARD, y, out, mode, work, stream)
 
     def adjoint(self, y: torch.Tensor, out: torch.Tensor | None = None, mode: str = "fused",
-                keep_input: bool = True, stream=None) -> torch.Tensor:
-        """F^H y (stage g -> stage 0): the backward passes with 1/N (complex-to-complex)."""
+                keep_input: bool = True, stream=None, coef: torch.Tensor | None = None) -> torch.Tensor:
+        """F^H y (stage g -> stage 0): the backward passes with 1/N (complex-to-complex);
+        times coef[()] (float64 0-d device tensor, read on the device) when given."""
         if out is None:
             out = self.empty_stage(0)
         work = self.workspace(mode, keep_input)
         wp = _ptr(work) if work is not None else ctypes.c_void_p(0)
         wb = work.numel() * work.element_size() if work is not None else 0
-        call("tfft_adjoint", self._h, _MODES[mode], _ptr(y), _ptr(out), wp, wb, _stream_ptr(stream))
+        cp = _ptr(coef) if coef is not None else ctypes.c_void_p(0)
+        call("tfft_adjoint", self._h, _MODES[mode], _ptr(y), _ptr(out), wp, wb, cp, _stream_ptr(stream))
         return out
 
     def weighted_energy(self, stage: int, y: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
-                        stream=None) -> torch.Tensor:
-        """sum |y * w|^2 over a stage buffer, as a float64 0-d device tensor."""
+                        stream=None, u: torch.Tensor | None = None) -> torch.Tensor:
+        """sum |y * w|^2 over a stage buffer, as a float64 0-d device tensor; with
+        ``u`` given, the same sweep also writes u = w^2 y into it."""
         if out is None:
             out = torch.empty((), dtype=torch.float64, device=y.device)
-        call("tfft_weighted_energy", self._h, stage, _ptr(y), _ptr(w), _ptr(out), _stream_ptr(stream))
+        up = _ptr(u) if u is not None else ctypes.c_void_p(0)
+        call("tfft_weighted_energy", self._h, stage, _ptr(y), _ptr(w), _ptr(out), up, _stream_ptr(stream))
         return out
 
     def weight_scale(self, stage: int, y: torch.Tensor, w: torch.Tensor, coef: torch.Tensor | None,

@@ -86,3 +86,34 @@ def test_weighted_energy_is_deterministic(cuda_device):
     assert vals[0] == vals[1] == vals[2]
     ref = float(np.sum(np.abs(y.cpu().numpy().astype(np.complex128)) ** 2 * w.cpu().numpy().astype(np.float64) ** 2))
     assert abs(vals[0] - ref) <= 1e-12 * ref
+
+
+def test_weighted_energy_writes_u(cuda_device):
+    """The loss sweep's second output u = w^2 y (also in place over y), the loss unchanged."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (32, 48, 40), (2, 4)
+    p = Plan(shape, grid, device=cuda_device)
+    y = to_dev(inputs.normal_complex(shape, seed=8).numpy().reshape(-1), cuda_device)
+    w = to_dev(inputs.uniform01_real(shape, seed=9).numpy().reshape(-1), cuda_device)
+    l0 = float(p.weighted_energy(2, y, w))
+    u = torch.empty_like(y)
+    l1 = float(p.weighted_energy(2, y, w, u=u))
+    assert l0 == l1
+    want = (w.double() ** 2) * y.to(torch.complex128)
+    assert float(torch.linalg.vector_norm(u.to(torch.complex128) - want) / torch.linalg.vector_norm(want)) <= 1e-7
+    y2 = y.clone()
+    l2 = float(p.weighted_energy(2, y2, w, u=y2))
+    assert l2 == l0 and torch.equal(y2, u)
+
+
+@pytest.mark.parametrize("mode", ["fused", "unfused", "packed"])
+def test_adjoint_device_coefficient(cuda_device, mode):
+    """adjoint(y, coef=c) = c * adjoint(y): the factor is read on the device by the last pass."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (32, 32, 32), (2, 2)
+    p = Plan(shape, grid, device=cuda_device)
+    y = to_dev(R.scatter(inputs.normal_complex(shape, seed=10).numpy(), grid, 2), cuda_device)
+    c = torch.tensor(-2.75, dtype=torch.float64, device=cuda_device)
+    a = p.adjoint(y, mode=mode)
+    b = p.adjoint(y, mode=mode, coef=c)
+    assert rel_l2(b.cpu().numpy(), -2.75 * a.cpu().numpy()) <= 1e-6
