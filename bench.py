@@ -171,7 +171,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if rank == 0 or world > 1:
         _build.build()
-    plan = Plan(SHAPE, GRID, device=dev, tma=not args.no_tma)
+    if args.profile_only and args.profile_workload != "fft":
+        profile_workload(args, dev)
+        return
+    plan = Plan(SHAPE, GRID, device=dev, tma=not args.no_tma, precision=args.precision)
     stream = torch.cuda.current_stream()
 
     # seeded input: complex N(0, 1), the same array on every replica
@@ -353,6 +356,41 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def profile_workload(args, dev):
+    """A short loop of one secondary workload for profiler captures (--profile-only)."""
+    import torch
+    from paper_1804_09536_gb300 import inputs
+    from paper_1804_09536_gb300.plan import Batch, Plan
+    if args.profile_workload == "batch":
+        problems = inputs.batch_problems(48, seed=0)[:args.batch_count]
+        plans = [Plan(sh, gr, device=dev) for sh, gr in problems]
+        b = Batch(plans, sign=-1)
+        for k, (sh, gr) in enumerate(problems):
+            b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(sh, seed=k).to(dev), 0))
+        one = b.execute
+    else:
+        from paper_1804_09536_gb300.autograd import spectral_weight_loss
+        plan = Plan(SHAPE, GRID, device=dev)
+        x = plan.scatter(inputs.normal_complex(SHAPE, seed=0).to(dev), 0).requires_grad_(True)
+        w = plan.scatter(inputs.uniform01_real(SHAPE, seed=1).to(dev), plan.g)
+
+        def one():
+            x.grad = None
+            spectral_weight_loss(x, w, plan).backward()
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        one()
+    e.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_only": True, "workload": args.profile_workload,
+                      "ms_per_step": a.elapsed_time(e) / args.steps}))
 
 
 def r2c_slab(plan_cls, dev, steps, barrier, tma=True):
@@ -663,7 +701,16 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="batch executor with default tiles")
     ap.add_argument("--profile-only", action="store_true",
                     help="headline loop only (no comparison paths, e2e or CPU baseline)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "fp16x3"],
+                    help="arithmetic of the length-512 contiguous passes in the headline loop")
+    ap.add_argument("--profile-workload", default="fft", choices=["fft", "batch", "loss"],
+                    help="with --profile-only: the loop to run (fft: the headline step; batch: the "
+                         "batch executor over the first --batch-count transforms; loss: the "
+                         "loss + gradient step)")
+    ap.add_argument("--batch-count", type=int, default=48)
     args = ap.parse_args()
+    if args.precision != "fp32" and not args.profile_only:
+        ap.error("--precision is for profiling runs (--profile-only); the headline is FP32")
     _set_workload(args.shape, args.grid)
     if args.warmup < 3:
         args.warmup = 3
