@@ -204,6 +204,28 @@ int tfft_adjoint(tfft_plan plan, int mode, const void *in, void *out, void *work
                  const double *d_coef, void *stream);
 
 /*
+ * Transforms of a sequence of arrays in page-locked host memory, with the
+ * copies overlapped: for k = 0 .. count-1, h_in[k] (stage 0 for a first
+ * forward, stage g for a first backward; real for an r2c forward) is copied
+ * to the GPU, the fused transforms signs[0], signs[1], ... (alternating
+ * directions, e.g. {-1, +1} = forward then inverse) run on it, and the result
+ * is copied back to h_out[k].  Arrays alternate between two device buffer
+ * sets carved from d_space (caller-allocated, device memory, 256-byte
+ * aligned, at least tfft_host_space_bytes): the copy-in of array k+1 and the
+ * copy-out of array k-1 run on two library-owned streams while array k is
+ * transformed on `stream`.  Stream-ordered: the work starts after what was
+ * queued on `stream` before the call, and `stream` waits for the last
+ * copy-out.  Host pointers that are not page-locked are rejected
+ * (TFFT_EINVAL: the copies could not overlap); h_in[k] is not modified.  The
+ * first call creates the two streams on the current device; later calls must
+ * use the same device.  Not for CUDA graph capture.  The paper has no
+ * counterpart (its arrays live in each rank's host memory).
+ */
+int tfft_host_space_bytes(tfft_plan plan, size_t *bytes);
+int tfft_execute_host(tfft_plan plan, int nsigns, const int *signs, int count, const void *const *h_in,
+                      void *const *h_out, void *d_space, size_t space_bytes, void *stream);
+
+/*
  * Spectral-weight loss sum_k |y_k w_k|^2 over a whole stage buffer: y is
  * complex64, w is float32 in the same layout (w[i] weighs y[i]); each term and
  * each thread's running sum are carried in compensated FP32 (about 48 bits),

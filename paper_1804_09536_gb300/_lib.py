@@ -57,6 +57,9 @@ SIGNATURES = {
     "tfft_plan_set_launch_events": [_vp, ctypes.POINTER(_vp), ctypes.c_int],
     "tfft_adjoint": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp, _vp],
     "tfft_weighted_energy": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "tfft_host_space_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
+    "tfft_execute_host": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(_vp),
+                          ctypes.POINTER(_vp), _vp, ctypes.c_size_t, _vp],
     "tfft_weight_scale": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, _vp, _vp],
     "tfft_batch_create": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.c_int],
     "tfft_batch_destroy": [_vp],

@@ -177,6 +177,29 @@ class Plan:
         call("tfft_adjoint", self._h, _MODES[mode], _ptr(y), _ptr(out), wp, wb, cp, _stream_ptr(stream))
         return out
 
+    def host_space_bytes(self) -> int:
+        """Device bytes tfft_execute_host needs (two buffer sets)."""
+        n = ctypes.c_size_t()
+        call("tfft_host_space_bytes", self._h, ctypes.byref(n))
+        return n.value
+
+    def execute_host(self, signs, h_ins, h_outs, space: torch.Tensor | None = None, stream=None):
+        """Transforms signs[0], signs[1], ... of every pinned host tensor in h_ins into the
+        matching tensor of h_outs, copies overlapped with the transforms (tfft_execute_host).
+        Asynchronous on ``stream``; returns the device space tensor (keep it alive until the
+        stream has reached this point)."""
+        if space is None:
+            space = torch.empty(self.host_space_bytes(), dtype=torch.uint8, device=self.device)
+        sg = (ctypes.c_int * len(signs))(*signs)
+        n = len(h_ins)
+        if len(h_outs) != n:
+            raise ValueError("h_ins and h_outs differ in length")
+        ins = (ctypes.c_void_p * n)(*[t.data_ptr() for t in h_ins])
+        outs = (ctypes.c_void_p * n)(*[t.data_ptr() for t in h_outs])
+        call("tfft_execute_host", self._h, len(signs), sg, n, ins, outs, _ptr(space),
+             space.numel() * space.element_size(), _stream_ptr(stream))
+        return space
+
     def weighted_energy(self, stage: int, y: torch.Tensor, w: torch.Tensor, out: torch.Tensor | None = None,
                         stream=None, u: torch.Tensor | None = None) -> torch.Tensor:
         """sum |y * w|^2 over a stage buffer, as a float64 0-d device tensor; with
