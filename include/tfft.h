@@ -113,9 +113,13 @@ int tfft_decompose(int64_t N, int64_t M, int64_t p, int64_t *n, int64_t *s);
  * (real input, Hermitian half on the last axis; N[d-1] even).  precision:
  * TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3.  flags: TFFT_NORM_FORWARD or
  * TFFT_NORM_BACKWARD, optionally | TFFT_NO_TMA.
- * Transforms need every length to factor into 2, 3 and 5 and be <= 4096;
- * a plan with other lengths is still created and redistributes, but its
- * tfft_execute() and tfft_partial() return TFFT_EUNSUPPORTED.
+ * Complex lengths that factor into 2, 3 and 5 (<= 4096) run mixed-radix
+ * Stockham passes; any other complex length <= 2048 runs Bluestein's
+ * convolution form of the DFT (two power-of-two FFTs of length >= 2N - 1 with
+ * FP64-built chirp tables) in the same pass structure.  Longer other lengths
+ * (and an r2c half-length without a 2/3/5 plan) leave the plan able to
+ * redistribute, but its tfft_execute() and tfft_partial() return
+ * TFFT_EUNSUPPORTED.
  * The plan is a host object; destroy it with tfft_plan_destroy().
  */
 int tfft_plan_create(tfft_plan *plan, int ndims, const int64_t *shape, int grid_ndims,

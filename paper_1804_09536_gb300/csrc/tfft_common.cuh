@@ -299,6 +299,7 @@ struct AxisPlan {
   int spec;        // 1: a compile-time specialised kernel exists for this plan
   int width;       // lines per CTA (contiguous) or tile width W (strided)
   int radix[MAXSTAGES];
+  int blue_m;      // > 0: length without a 2/3/5 plan, done by Bluestein with this convolution length
 };
 
 TFFT_HD int stage_radix(uint64_t code, int s) { return (int)((code >> (5 * s)) & 31); }

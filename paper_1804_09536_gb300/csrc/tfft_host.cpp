@@ -1,6 +1,8 @@
 // Host side of the C ABI (include/tfft.h): plan construction on the virtual
 // process grid, state image, pass lists and launches.
 #include <algorithm>
+#include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
@@ -111,6 +113,12 @@ struct tfft_plan_s {
   std::map<int, AxisPlan> aplan;   // contiguous-line passes
   std::map<int, AxisPlan> aplan_s; // strided passes
   std::map<int, size_t> tw_off;
+  struct BlueH {       // Bluestein lengths: convolution plan and the offsets of their tables
+    int M = 0;
+    AxisPlan apm{};
+    size_t chirp_off = 0, bhat_off = 0;
+  };
+  std::map<int, BlueH> blue;
   std::map<std::tuple<int, int, int>, std::pair<size_t, int64_t>> colblocks;  // (lin,lout,W)
   std::map<std::pair<int, int>, ExchangeBoxes> xboxes;                       // (from,to)
   std::map<std::pair<int, int>, std::vector<size_t>> xbox_off;  // direct, pack, xchg, unpack
@@ -201,8 +209,7 @@ DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
 // `strided`: the line is one column of a W-wide tile of at most 512 threads,
 // so plans with at most 32 threads per line (W >= 16 columns) are preferred.
 bool make_axis_plan(int L, bool strided, AxisPlan& best) {
-  best.spec = 0;
-  best.width = 0;
+  best = AxisPlan{};
   if (L == 1) {
     best = AxisPlan{1, 1, 1, 0, 0, 0, 1, {}};
     return true;
@@ -288,9 +295,10 @@ bool make_axis_plan(int L, bool strided, AxisPlan& best) {
 int strided_width(const AxisPlan& ap) {
   if (ap.spec) return ap.width;
   int W = std::max(1, std::min(32, 512 / ap.T));
-  // shared memory: L x W elements (two buffers for the generic kernel) + row tables
+  // shared memory: L x W elements (two buffers for the generic kernel; two of
+  // the convolution length for Bluestein) + row tables
   const size_t budget = 200 * 1024 - 16 * (size_t)ap.L;
-  const size_t per_col = (ap.E == 0 ? 2 : 1) * 8 * (size_t)ap.L;
+  const size_t per_col = ap.blue_m ? 2 * 8 * (size_t)ap.blue_m : (ap.E == 0 ? 2 : 1) * 8 * (size_t)ap.L;
   while (W > 1 && (size_t)W * per_col > budget) --W;
   return W;
 }
@@ -751,6 +759,8 @@ int check_ptr(const void* ptr, const char* name) {
   return TFFT_OK;
 }
 
+BlueArgs blue_args(tfft_plan p, int N);
+
 int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) {
   const float2* in = static_cast<const float2*>(bufs[s.src]);
   float2* out = static_cast<float2*>(bufs[s.dst]);
@@ -768,7 +778,9 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.coef = s.coef;
     a.status = reinterpret_cast<int*>(p->d_state);
     a.wait_limit = p->wait_limit;
-    if (p->precision != TFFT_FP32 && tc_supported(a.ap.L))
+    if (a.ap.blue_m)
+      e = launch_contig_blue(a, blue_args(p, s.L), st);
+    else if (p->precision != TFFT_FP32 && tc_supported(a.ap.L))
       e = launch_contig_tc(a, p->precision, st);
     else
       e = launch_contig(a, st);
@@ -814,6 +826,10 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
         e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
         done = true;
       }
+    }
+    if (!done && a.ap.blue_m) {
+      e = launch_strided_blue(a, blue_args(p, s.L), st);
+      done = true;
     }
     if (!done) e = launch_strided(a, st);
   } else if (s.kind == S_REAL) {
@@ -865,6 +881,68 @@ bool is_smooth_235(int64_t n) {
   for (int f : {2, 3, 5})
     while (n % f == 0) n /= f;
   return n == 1;
+}
+
+// Bluestein plan for a length N without a 2/3/5 factorisation: convolution
+// length M = the power of two >= 2N - 1 (at most MAXLEN), and the tables,
+// evaluated in double and rounded once: chirp[n] = exp(-i pi (n^2 mod 2N) / N)
+// and bhat = FFT_M(b) / M for the wrapped filter b[m] = b[M - m] = conj(chirp[m]).
+bool make_bluestein(tfft_plan p, int N) {
+  int M = 1;
+  while (M < 2 * N - 1) M <<= 1;
+  AxisPlan apm{};
+  if (M > MAXLEN || !make_axis_plan(M, false, apm)) return false;
+  const double pi = 3.14159265358979323846;
+  std::vector<float2> chirp(N), bhat(M);
+  std::vector<std::complex<double>> b(M, 0.0), w(M);
+  for (int n = 0; n < N; ++n) {
+    const int64_t r = ((int64_t)n * n) % (2 * (int64_t)N);
+    const double ang = pi * (double)r / (double)N;
+    chirp[n] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    b[n] = std::complex<double>(std::cos(ang), std::sin(ang));
+    if (n > 0) b[M - n] = b[n];
+  }
+  for (int m = 0; m < M; ++m) w[m] = std::polar(1.0, -2.0 * pi * (double)m / (double)M);
+  std::vector<int> nz;
+  for (int m = 0; m < M; ++m)
+    if (b[m] != 0.0) nz.push_back(m);
+  for (int k = 0; k < M; ++k) {
+    std::complex<double> acc = 0.0;
+    for (int m : nz) acc += b[m] * w[((int64_t)m * k) % M];
+    acc /= (double)M;
+    bhat[k] = make_float2((float)acc.real(), (float)acc.imag());
+  }
+  tfft_plan_s::BlueH h;
+  h.M = M;
+  h.apm = apm;
+  h.chirp_off = image_add(p, chirp.data(), chirp.size() * sizeof(float2));
+  h.bhat_off = image_add(p, bhat.data(), bhat.size() * sizeof(float2));
+  if (!p->tw_off.count(M)) p->tw_off[M] = image_add(p, nullptr, (size_t)M * sizeof(float2));
+  if (!p->tw_off.count(N)) p->tw_off[N] = image_add(p, nullptr, (size_t)N * sizeof(float2));
+  AxisPlan ap{};
+  ap.L = N;
+  ap.E = 0;
+  ap.T = apm.T;
+  ap.blue_m = M;
+  ap.width = std::max(1, std::min(4096 / M, 512 / apm.T));  // lines per CTA (two M-buffers each)
+  AxisPlan aps = ap;
+  aps.width = strided_width(aps);
+  p->aplan[N] = ap;
+  p->aplan_s[N] = aps;
+  p->blue[N] = h;
+  return true;
+}
+
+BlueArgs blue_args(tfft_plan p, int N) {
+  const tfft_plan_s::BlueH& h = p->blue.at(N);
+  BlueArgs b;
+  b.N = N;
+  b.M = h.M;
+  b.apm = h.apm;
+  b.twm = reinterpret_cast<const float2*>(p->d_state + p->tw_off.at(h.M));
+  b.chirp = reinterpret_cast<const float2*>(p->d_state + h.chirp_off);
+  b.bhat = reinterpret_cast<const float2*>(p->d_state + h.bhat_off);
+  return b;
 }
 
 }  // namespace
@@ -981,7 +1059,11 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     if (kind == TFFT_R2C && m == ndims - 1) break;  // the innermost axis is the real pass
     const int L = (int)p->cshape[m];
     if (p->aplan.count(L)) continue;
-    AxisPlan ap, aps;
+    AxisPlan ap{}, aps{};
+    if (!is_smooth_235(L) && L <= MAXLEN / 2) {
+      if (!make_bluestein(p, L)) p->transformable = false;
+      continue;
+    }
     if (L > MAXLEN || !is_smooth_235(L) || !make_axis_plan(L, false, ap) ||
         !make_axis_plan(L, true, aps)) {
       p->transformable = false;
@@ -1164,7 +1246,7 @@ int tfft_partial(tfft_plan p, int stage, int axis, int sign, void* inout, void* 
 
 int tfft_plan_num_launches(tfft_plan p, int sign, int mode, int* n) {
   if (!p || !n) return fail(TFFT_EINVAL, "NULL argument");
-  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length is not a product of 2, 3, 5 up to 4096");
+  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
   auto it = p->steps.find({sign, mode});
   if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
   *n = (int)it->second.size();
@@ -1174,7 +1256,7 @@ int tfft_plan_num_launches(tfft_plan p, int sign, int mode, int* n) {
 int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name, int name_len,
                           int64_t* bytes) {
   if (!p || !bytes || (name_len > 0 && !name)) return fail(TFFT_EINVAL, "NULL argument");
-  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length is not a product of 2, 3, 5 up to 4096");
+  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
   auto it = p->steps.find({sign, mode});
   if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
   if (index < 0 || index >= (int)it->second.size()) return fail(TFFT_EINVAL, "launch index out of range");
@@ -1419,7 +1501,7 @@ static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in
   if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
   if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
   if (mode < TFFT_MODE_FUSED || mode > TFFT_MODE_PACKED) return fail(TFFT_EINVAL, "unknown mode");
-  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length is not a product of 2, 3, 5 up to 4096");
+  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
   int rc = check_ptr(in, "in");
   if (rc) return rc;
   rc = check_ptr(out, "out");
@@ -1532,7 +1614,7 @@ std::vector<int> batch_candidates(int kind, int L) {
   std::vector<int> v;
   for (int id = 0; id < batch_num_variants(); ++id) {
     int k, l, e, bw;
-    AxisPlan ap;
+    AxisPlan ap{};
     if (batch_variant(id, k, l, e, bw, ap) && k == kind && l == L) v.push_back(id);
   }
   return v;
@@ -1553,7 +1635,7 @@ int batch_upload(tfft_batch b, cudaStream_t st) {
     const Step& s = b->steps[h.t][h.pass];
     const int v = b->choice[{h.kind, h.L}];
     int k, l, e, bw;
-    AxisPlan ap;
+    AxisPlan ap{};
     batch_variant(v, k, l, e, bw, ap);
     void* bufs[4] = {b->ins[h.t], b->outs[h.t], b->works[h.t], nullptr};
     BatchSeg& D = dsegs[i];
@@ -1693,7 +1775,7 @@ int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int si
     if (h.kind == 1)
       for (int v : batch_candidates(1, s.L)) {
         int k, l, e, bw;
-        AxisPlan ap;
+        AxisPlan ap{};
         batch_variant(v, k, l, e, bw, ap);
         h.cb_cap = std::max(h.cb_cap, colblock_list(b->plans[t], s.lin, s.lout, bw).size());
       }

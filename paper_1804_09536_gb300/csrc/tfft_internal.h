@@ -29,6 +29,17 @@ struct ContigArgs {
   uint32_t wait_limit;  // polls of a bounded copy wait (TMA passes)
 };
 
+// Bluestein's algorithm for a line length N without a 2/3/5 factorisation:
+// the DFT as a circular convolution of length M (a power of two >= 2N - 1)
+// with a chirp, done with two length-M FFTs.
+struct BlueArgs {
+  int N, M;
+  AxisPlan apm;          // length-M FFT plan (shared-memory stages)
+  const float2* twm;     // the M roots exp(-2 pi i m / M)
+  const float2* chirp;   // N values exp(-i pi (n^2 mod 2N) / N)
+  const float2* bhat;    // M values: the FFT of the wrapped chirp filter, times 1 / M
+};
+
 #ifdef __CUDACC__
 // Output factor of a contiguous pass: the host's scale, times the device
 // coefficient when there is one (formed in double, applied in float).
@@ -119,6 +130,8 @@ struct BoxArgs {
 cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s);
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
 cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s);
+cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStream_t s);
+cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
 
 // Batched persistent executor (tfft_batch.cu).  One segment = the tiles of

@@ -359,6 +359,109 @@ __global__ void __launch_bounds__(512) k_fft_strided_generic(const StridedArgs a
   }
 }
 
+// ------------------------------------------------------------ Bluestein
+//
+// A line of length N with no 2/3/5 factorisation: with c[n] = exp(i pi n^2 / N),
+// X[k] = conj(c[k]) * sum_n (x[n] conj(c[n])) c[k - n], a circular
+// convolution once a = x conj(c) is zero-padded to M >= 2N - 1 and c is
+// wrapped around (b[m] = b[M - m] = c[m]).  The convolution is done as
+// FFT_M(a) * (FFT_M(b) / M) followed by an inverse FFT, taken as
+// conj o FFT_M o conj.
+
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// Convolution of the chirped, zero-padded column (stride, cx) held in b0;
+// returns the buffer (b0 or b1) holding conj(a (*) b).
+__device__ __forceinline__ float2* blue_convolve(float2* b0, float2* b1, const BlueArgs& b, int jt, int T,
+                                                 int stride, int cx) {
+  float2* r = generic_fft(b0, b1, b.apm, jt, stride, cx, b.twm);
+  for (int i = jt; i < b.M; i += T) r[i * stride + cx] = cconj(cmul(r[i * stride + cx], __ldg(&b.bhat[i])));
+  __syncthreads();
+  return generic_fft(r, r == b0 ? b1 : b0, b.apm, jt, stride, cx, b.twm);
+}
+
+__global__ void __launch_bounds__(512) k_blue_contig(const ContigArgs a, const BlueArgs b) {
+  const float oscale = contig_scale(a);
+  extern __shared__ float2 smem[];
+  const int N = b.N, M = b.M, T = b.apm.T;
+  const int jt = threadIdx.x, ly = threadIdx.y, B = blockDim.y;
+  float2* b0 = smem + (size_t)ly * M;
+  float2* b1 = smem + (size_t)(B + ly) * M;
+  const bool inv = a.sign > 0;
+  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
+    const int64_t line = base + ly;
+    const bool act = line < a.nlines;
+    __syncthreads();
+    for (int i = jt; i < M; i += T) {
+      float2 v = make_float2(0.f, 0.f);
+      if (act && i < N) {
+        v = a.in[line * N + i];
+        if (inv) v.y = -v.y;
+        v = cmul(v, __ldg(&b.chirp[i]));
+      }
+      b0[i] = v;
+    }
+    __syncthreads();
+    const float2* r = blue_convolve(b0, b1, b, jt, T, 1, 0);
+    for (int k = jt; k < N; k += T) {
+      float2 y = cscale(cmul(cconj(r[k]), __ldg(&b.chirp[k])), oscale);
+      if (inv) y.y = -y.y;
+      if (act) a.out[line * N + k] = y;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(512) k_blue_strided(const StridedArgs a, const BlueArgs b) {
+  extern __shared__ float2 smem[];
+  const int N = b.N, M = b.M, T = b.apm.T, W = a.W;
+  const int cx = threadIdx.x, jt = threadIdx.y;
+  const int tid = jt * W + cx, nthr = W * T;
+  float2* b0 = smem;
+  float2* b1 = smem + (size_t)M * W;
+  int64_t* rin = reinterpret_cast<int64_t*>(smem + 2 * (size_t)M * W);
+  int64_t* rout = rin + N;
+  const bool inv = a.sign > 0;
+  const int64_t ntiles = a.nouter * a.ncolblocks;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t o = tile / a.ncolblocks;
+    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
+    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
+    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    __syncthreads();
+    for (int i = tid; i < N; i += nthr) {
+      int64_t g[MAXD];
+#pragma unroll
+      for (int m = 0; m < MAXD; ++m)
+        g[m] = (m == a.axis) ? (int64_t)i
+             : (m == a.d - 1) ? (int64_t)blk.x
+             : (m == a.oax0) ? go0
+             : (m == a.oax1) ? go1
+                             : 0;
+      rin[i] = layout_addr(a.lin, g[0], g[1], g[2], g[3]);
+      rout[i] = layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < M * W; idx += nthr) {
+      const int pos = idx / W, c = idx - (idx / W) * W;
+      float2 v = make_float2(0.f, 0.f);
+      if (pos < N && c < blk.y) {
+        v = a.in[rin[pos] + c];
+        if (inv) v.y = -v.y;
+        v = cmul(v, __ldg(&b.chirp[pos]));
+      }
+      b0[idx] = v;
+    }
+    __syncthreads();
+    const float2* r = blue_convolve(b0, b1, b, jt, T, W, cx);
+    for (int idx = tid; idx < N * W; idx += nthr) {
+      const int pos = idx / W, c = idx - (idx / W) * W;
+      float2 y = cscale(cmul(cconj(r[idx]), __ldg(&b.chirp[pos])), a.scale);
+      if (inv) y.y = -y.y;
+      if (c < blk.y) a.out[rout[pos] + c] = y;
+    }
+  }
+}
+
 // ------------------------------------------------------------ box copy
 
 __global__ void __launch_bounds__(256) k_boxcopy(const BoxArgs a) {
@@ -506,6 +609,29 @@ cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStream_t s) {
+  static cudaError_t attr = allow_smem(k_blue_contig);
+  if (attr != cudaSuccess) return attr;
+  const int B = a.lines_per_cta;
+  const size_t smem = 2 * (size_t)B * b.M * sizeof(float2);
+  int64_t grid = (a.nlines + B - 1) / B;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaSuccess;
+  k_blue_contig<<<(unsigned)grid, dim3(b.apm.T, B), smem, s>>>(a, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStream_t s) {
+  static cudaError_t attr = allow_smem(k_blue_strided);
+  if (attr != cudaSuccess) return attr;
+  const size_t smem = 2 * (size_t)b.M * a.W * sizeof(float2) + 2 * (size_t)b.N * sizeof(int64_t);
+  int64_t grid = a.nouter * a.ncolblocks;
+  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid < 1) return cudaSuccess;
+  k_blue_strided<<<(unsigned)grid, dim3(a.W, b.apm.T), smem, s>>>(a, b);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s) {

@@ -72,10 +72,11 @@ def test_plan_layouts_match_oracle(lib, shape, grid):
 def test_unsupported_and_invalid(lib):
     from paper_1804_09536_gb300.plan import Plan
     from paper_1804_09536_gb300._lib import TfftError
-    p = Plan((7, 8, 8), (2, 2), bind=False)  # prime length: plans and redistributes ...
+    p = Plan((4099, 8, 8), (2, 2), bind=False)  # prime length above 2048: plans and redistributes ...
     with pytest.raises(TfftError) as e:
-        p.num_launches(-1)                     # ... but does not transform
+        p.num_launches(-1)                        # ... but does not transform
     assert e.value.status == 2
+    assert Plan((7, 127, 8), (2, 2), bind=False).num_launches(-1) == 3  # Bluestein lengths do
     with pytest.raises(TfftError) as e:
         Plan((8, 8, 8), (2, 2, 2), bind=False)
     assert e.value.status == 1  # grid_ndims > ndims - 1 (Sec. 3.6)
