@@ -544,8 +544,16 @@ bool tma_geo(tfft_plan p, int stage, int axis, int W, TmaGeo& G) {
     G.rdim[m] = G.cut[m] ? 3 + (p->g - 1 - S.owner[m]) : 0;
   }
   if (G.n[2] % W != 0 || (W & 1)) return false;
+  G.split = 0;
+  for (int m = 0; m < 3; ++m) G.rmul[m] = G.cut[m] ? (int)p->rstride[S.owner[m]] : 0;
   if (G.cut[axis]) {
     if (G.n[axis] > 256 || p->grid[S.owner[axis]] > 256) return false;
+    G.nops = 1;
+    G.rows_per_op = L;
+  } else if (L > 256 && L % 256 == 0 && L / 256 <= 256 && axis != 2) {
+    // one copy per tile: measured, 2 / 4 / 8 copies of 256 / 128 / 64 rows
+    // made the 512-row pass take 0.39 / 0.50 / 0.74 ms
+    G.split = 1;
     G.nops = 1;
     G.rows_per_op = L;
   } else {
@@ -581,7 +589,21 @@ bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void*
   cuuint64_t strides[4] = {(cuuint64_t)G.n[2] * 8, (cuuint64_t)G.n[1] * G.n[2] * 8, (cuuint64_t)local * 8,
                            (cuuint64_t)local * 8 * D3};
   cuuint32_t box[5] = {(cuuint32_t)W, 1, 1, 1, 1};
-  if (G.cut[axis]) {
+  if (G.split) {  // [rank][outer][axis / 256][256][n2], see TmaGeo
+    const int tax = 1 - axis;  // the other non-innermost axis (d == 3)
+    const int64_t sa = axis == 0 ? (int64_t)G.n[1] * G.n[2] : G.n[2];
+    const int64_t so = tax == 0 ? (int64_t)G.n[1] * G.n[2] : G.n[2];
+    dims[1] = 256;
+    dims[2] = (cuuint64_t)(G.n[axis] / 256);
+    dims[3] = (cuuint64_t)G.n[tax];
+    dims[4] = (cuuint64_t)p->nranks;
+    strides[0] = (cuuint64_t)sa * 8;
+    strides[1] = (cuuint64_t)sa * 256 * 8;
+    strides[2] = (cuuint64_t)so * 8;
+    strides[3] = (cuuint64_t)local * 8;
+    box[1] = 256;
+    box[2] = (cuuint32_t)(G.n[axis] / 256);
+  } else if (G.cut[axis]) {
     box[2 - axis] = (cuuint32_t)G.n[axis];                             // local rows
     box[G.rdim[axis]] = (cuuint32_t)(p->cshape[axis] / G.n[axis]);     // every rank of the subgroup
   } else {

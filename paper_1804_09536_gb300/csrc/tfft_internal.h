@@ -104,6 +104,11 @@ struct TmaGeo {
   int rdim[3];
   int nops;
   int rows_per_op;
+  // split view (uncut FFT axis longer than a 256-row box): the 5-D array is
+  // [rank][outer axis][axis / 256][256][n2] with the rank as one linear index,
+  // so that a whole tile is one copy; rmul[m] = rank stride of cut axis m
+  int split;
+  int rmul[3];
 };
 
 // Copy of rectangular boxes: each box has up to MAXD extents, a source and a

@@ -114,6 +114,14 @@ __device__ __forceinline__ void tile_coords(const TmaGeo& G, int axis, int k, in
                                             int tax, int (&c)[5]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) c[i] = 0;
+  if (G.split) {  // [rank][outer][axis / 256][256][n2]: the whole tile is op 0
+    const int64_t pc = G.cut[2] ? col / G.n[2] : 0;
+    const int64_t po = G.cut[tax] ? gt / G.n[tax] : 0;
+    c[0] = (int)(col - pc * G.n[2]);
+    c[3] = (int)(gt - po * G.n[tax]);
+    c[4] = (int)(pc * G.rmul[2] + po * G.rmul[tax]);
+    return;
+  }
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     int64_t g = (m == axis) ? (int64_t)k * G.rows_per_op : (m == 2) ? col : (m == tax) ? gt : 0;
