@@ -117,3 +117,32 @@ def test_adjoint_device_coefficient(cuda_device, mode):
     a = p.adjoint(y, mode=mode)
     b = p.adjoint(y, mode=mode, coef=c)
     assert rel_l2(b.cpu().numpy(), -2.75 * a.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.slow
+def test_full_size_512_loss_and_gradient_properties(cuda_device):
+    """The differentiable workload of bench.py (512^3, 4 x 8), through the properties that
+    hold at any size: the loss equals sum w^2 |F x|^2 formed in double from the forward
+    output (whose samples the FFT tests pin to the oracle); the gradient equals
+    2 F^H(w^2 F x) assembled from the separate calls; the adjoint identity
+    <F x, z> = <x, F^H z> for a random z."""
+    from paper_1804_09536_gb300.autograd import spectral_weight_loss
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (512, 512, 512), (4, 8)
+    p = Plan(shape, grid, device=cuda_device)
+    x = p.scatter(inputs.normal_complex(shape, seed=0).to(cuda_device), 0)
+    w = p.scatter(inputs.uniform01_real(shape, seed=1).to(cuda_device), 2)
+    xr = x.clone().requires_grad_(True)
+    L = spectral_weight_loss(xr, w, p)
+    L.backward()
+    y = p.forward(x)
+    want_L = float(torch.sum(w.double() ** 2 * torch.abs(y.to(torch.complex128)) ** 2))
+    assert abs(float(L.detach()) - want_L) <= 1e-9 * want_L
+    z = p.adjoint(((w * w) * y).contiguous())
+    g = xr.grad.detach()
+    assert float(torch.linalg.vector_norm((g - 2 * z).to(torch.complex128)) /
+                 torch.linalg.vector_norm((2 * z).to(torch.complex128))) <= 1e-6
+    zr = p.scatter(inputs.normal_complex(shape, seed=2).to(cuda_device), 2)
+    lhs = torch.vdot(y.to(torch.complex128), zr.to(torch.complex128))
+    rhs = torch.vdot(x.to(torch.complex128), p.adjoint(zr).to(torch.complex128))
+    assert float(torch.abs(lhs - rhs)) <= 1e-5 * float(torch.abs(lhs))

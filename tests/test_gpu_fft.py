@@ -271,3 +271,33 @@ def test_c2r_ignores_dc_and_nyquist_imaginary_parts(cuda_device):
     z = p.inverse(to_dev(R.scatter(pert, grid, 1), cuda_device))
     want = dft.irfftn_backward(pert.astype(np.complex128), shape[-1])
     assert rel_l2(p.gather(z, 0, real=True).cpu().numpy(), want) <= RTOL_FP32
+
+
+@pytest.mark.slow
+def test_full_size_r2c_256_slab_sampled(cuda_device):
+    """The r2c slab workload of bench.py (256^3 real on 8 ranks): sampled outputs of the
+    Hermitian half against the oracle's definition (the c2c transform of the real input),
+    the real Parseval relation and the c2r round trip."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (256, 256, 256), (8,)
+    x = inputs.normal_real(shape, seed=0)
+    p = Plan(shape, grid, kind="r2c", device=cuda_device)
+    b0 = p.scatter(x.to(cuda_device), 0, real=True)
+    y = p.forward(b0)
+    yg = p.gather(y, 1).cpu().numpy()
+    assert yg.shape == (256, 256, 129)
+    rng = np.random.default_rng(2)
+    ks = [(0, 0, 0), (255, 255, 128), (1, 2, 3), (7, 0, 128)] + [
+        (int(rng.integers(0, 256)), int(rng.integers(0, 256)), int(rng.integers(0, 129))) for _ in range(4)]
+    want = dft.forward_at(x.numpy().astype(np.complex64), ks)
+    got = np.array([yg[k] for k in ks])
+    rms = float(np.sqrt(np.mean(np.abs(yg.astype(np.complex128)) ** 2)))
+    assert np.max(np.abs(got - want)) <= 1e-4 * rms
+    # Parseval over the full spectrum: columns 1..127 stand for two conjugate columns
+    n = x.numel()
+    e_in = float(torch.sum(x.to(torch.float64) ** 2)) / n
+    p2 = np.abs(yg.astype(np.complex128)) ** 2
+    e_out = float(p2[..., 0].sum() + p2[..., 128].sum() + 2 * p2[..., 1:128].sum())
+    assert abs(e_out - e_in) <= 1e-5 * e_in
+    back = p.inverse(y.clone())
+    assert float(torch.linalg.vector_norm((back - b0).double()) / torch.linalg.vector_norm(b0.double())) <= RTOL_FP32

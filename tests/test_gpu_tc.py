@@ -67,3 +67,31 @@ def test_tc_wait_expiry_reports_status(cuda_device):
     assert p.device_status() == 0
     want = dft.fftn_forward(x.cpu().numpy().reshape(shape).astype(np.complex128)).reshape(-1)
     assert rel_l2(y.cpu().numpy(), want) <= BARS["bf16x3"]
+
+
+@pytest.mark.slow
+def test_tc_full_size_512_sampled(cuda_device):
+    """The tensor-core workload of bench.py (512^3, 4 x 8): sampled outputs of both split
+    modes against the oracle's definition (error relative to the spectrum's rms), and the
+    round trip."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (512, 512, 512), (4, 8)
+    x = inputs.normal_complex(shape, seed=0)
+    rng = np.random.default_rng(3)
+    ks = [(0, 0, 0), (511, 511, 511), (5, 6, 7)] + [tuple(int(v) for v in rng.integers(0, 512, 3))
+                                                   for _ in range(3)]
+    want = dft.forward_at(x.numpy(), ks)
+    for precision in ("bf16x3", "fp16x3"):
+        p = Plan(shape, grid, device=cuda_device, precision=precision)
+        b0 = p.scatter(x.to(cuda_device), 0)
+        y = p.forward(b0)
+        torch.cuda.synchronize()
+        assert p.device_status() == 0
+        yg = p.gather(y, 2).cpu().numpy()
+        rms = float(np.sqrt(np.mean(np.abs(yg.astype(np.complex128)) ** 2)))
+        got = np.array([yg[k] for k in ks])
+        assert np.max(np.abs(got - want)) <= 20 * BARS[precision] * rms, precision
+        back = p.inverse(y)
+        d = torch.linalg.vector_norm((back - b0).to(torch.complex128)) / torch.linalg.vector_norm(b0.to(torch.complex128))
+        assert float(d) <= 2 * BARS[precision], precision
+        del p, b0, y, back
