@@ -176,6 +176,11 @@ constexpr int kRows = kLines * 32;                 // 256 sub-transforms per til
 constexpr uint32_t kOpBytes = (kRows / 8) * kSBO;  // one 256 x 32 16-bit operand
 constexpr uint32_t kBBytes = (32 / 8) * kSBO;      // the 32 x 32 DFT operand
 constexpr uint32_t kTmemCols = 64;                 // two FP32 groups of 32 columns
+// The stage-2 twiddles w^(jt r1) of the 512-root table, kept in shared memory
+// with one spare slot every 16: a half-warp reads indices jt * r1 (stride r1),
+// which would otherwise put up to 16 lanes on one bank for even r1.
+constexpr int kTwSlots = 512 + 512 / 16;
+__device__ __forceinline__ int tw_slot(int i) { return i + (i >> 4); }
 constexpr int kCtasPerSm = 4;                      // 4 x 64 of the 512 tensor-memory columns
 static_assert(kCtasPerSm * kTmemCols <= 512, "tensor memory columns per SM");
 
@@ -186,7 +191,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
   uint8_t* a_lo = sm + kOpBytes;
   uint8_t* b_hi = sm + 2 * kOpBytes;
   uint8_t* b_lo = b_hi + kBBytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(b_lo + kBBytes);
+  float2* s_tw = reinterpret_cast<float2*>(b_lo + kBBytes);  // the twiddles jt * r1 < 512, padded
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_tw + kTwSlots);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const int jt = tid % kT, ly = tid / kT;
@@ -207,6 +213,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
     *reinterpret_cast<uint16_t*>(b_hi + op_off(o, k)) = h;
     *reinterpret_cast<uint16_t*>(b_lo + op_off(o, k)) = l;
   }
+  for (int i = tid; i < kL; i += kThreads) s_tw[tw_slot(i)] = __ldg(&a.tw[i]);
   if (tid == 0) {
     mbar_init1(bar);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
     // exp(-2 pi i jt r1 / 512), then the A rows (line, r1), columns 2 jt, 2 jt + 1
 #pragma unroll
     for (int r1 = 0; r1 < kE; ++r1) {
-      const float2 t = (jt * r1 == 0) ? v[r1] : cmul(v[r1], __ldg(&a.tw[jt * r1]));
+      const float2 t = (jt * r1 == 0) ? v[r1] : cmul(v[r1], s_tw[tw_slot(jt * r1)]);
       uint32_t lo;
       const uint32_t hi = Half16<FMT>::pack_hi_lo(t.x, t.y, lo);
       const uint32_t off = op_off(ly * 32 + r1, 2 * jt);
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
 
 template <int FMT>
 cudaError_t run_tc(const ContigArgs& a, cudaStream_t s) {
-  const size_t smem = 2 * kOpBytes + 2 * kBBytes + 16;
+  const size_t smem = 2 * kOpBytes + 2 * kBBytes + kTwSlots * sizeof(float2) + 16;
   static cudaError_t attr =
       cudaFuncSetAttribute(k_contig_tc512<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (attr != cudaSuccess) return attr;
