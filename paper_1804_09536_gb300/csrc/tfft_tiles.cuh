@@ -1,7 +1,8 @@
 // Device-side building blocks of the compile-time specialised passes: the
-// Stockham stage, shared-memory helpers and the per-tile bodies of the
-// contiguous and strided passes.  Included by the pass kernels
-// (tfft_spec.cu) and by the batched executor (tfft_batch.cu).
+// Stockham stage, register-held stage twiddles, shared-memory helpers and the
+// per-tile bodies of the contiguous and strided passes.  Included by the pass
+// kernels (tfft_spec.cu, tfft_tma.cu, tfft_tc.cu) and by the batched executor
+// (tfft_batch.cu).
 #pragma once
 
 #include <type_traits>
