@@ -315,6 +315,7 @@ int tfft_plan_set_launch_events(tfft_plan plan, void *const *events, int count);
  * The paper has no batched executor; each transform follows its plan's steps.
  */
 typedef struct tfft_batch_s *tfft_batch;
+/* tfft_batch_bind's d_state must be 256-byte aligned (it holds TMA tensor maps). */
 int tfft_batch_create(tfft_batch *batch, int count, const tfft_plan *plans, int sign);
 int tfft_batch_destroy(tfft_batch batch);
 int tfft_batch_state_bytes(tfft_batch batch, size_t *bytes);
@@ -329,6 +330,12 @@ int tfft_batch_num_items(tfft_batch batch, int64_t *items, int *segments);
 int tfft_batch_segment(tfft_batch batch, int index, int *transform, int *pass);
 /* Executor tile variant chosen for passes of `kind` (0 contiguous, 1 strided) and length L. */
 int tfft_batch_variant(tfft_batch batch, int kind, int L, int *variant);
+/* Choose that variant by hand (one of the compiled candidates for kind and L,
+   else TFFT_EINVAL) and rewrite the bound state; synchronises.  A strided
+   TMA-staged variant applies to the segments whose layouts allow it (equal
+   blocks, 16-byte aligned tile columns); the others of that length run the
+   first plain variant. */
+int tfft_batch_set_variant(tfft_batch batch, int kind, int L, int variant, void *stream);
 /* Clock cycles a batch tile may wait for the previous pass (0: default ~2 s);
    a tiny value makes the waits expire on purpose (error-path tests). */
 int tfft_batch_set_wait_limit(tfft_batch batch, long long cycles);

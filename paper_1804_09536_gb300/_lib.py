@@ -71,6 +71,7 @@ SIGNATURES = {
     "tfft_batch_num_items": [_vp, _i64p, ctypes.POINTER(ctypes.c_int)],
     "tfft_batch_variant": [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "tfft_batch_segment": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+    "tfft_batch_set_variant": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "tfft_batch_set_wait_limit": [_vp, ctypes.c_longlong],
     "tfft_plan_set_wait_limit": [_vp, ctypes.c_uint32],
     "tfft_batch_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],

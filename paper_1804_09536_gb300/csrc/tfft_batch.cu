@@ -10,13 +10,20 @@
 // in order, so the item a CTA waits for was taken earlier by a running CTA:
 // the waits always end.  Each wait is bounded anyway: past the limit the CTA
 // records TFFT_DEVICE_ETIMEOUT, raises the launch's abort flag and leaves.
+//
+// Strided segments whose layouts have equal blocks can run TMA-staged tiles:
+// within an item the copy of tile i+1 runs while tile i is transformed (two
+// tile buffers), loads and stores are one cp.async.bulk.tensor each, and the
+// item is published only after its stores have completed.
 #include "tfft_tiles.cuh"
+#include "tfft_tma.cuh"
 
 namespace tfft {
 
 namespace {
 
 using namespace tiles;
+using namespace tma;
 
 // Tile variants the executor can run, all with 256 threads per CTA:
 // id, kind (0 contiguous / 1 strided), length, elements per thread,
@@ -38,7 +45,135 @@ using namespace tiles;
   X(13, 1, 256, 8, 8, 8, 8, 4)          \
   X(14, 1, 128, 8, 16, 8, 8, 2)
 
+// TMA-staged strided variants: id, length, elements per thread, tile width
+// (W * L / E = 256 threads), radices.
+#define TFFT_BATCH_TMA_VARIANTS(X) \
+  X(15, 64, 8, 32, 8, 8)           \
+  X(16, 128, 16, 32, 16, 8)        \
+  X(17, 256, 16, 16, 16, 16)
+
 constexpr int kBatchThreads = 256;
+
+// Bounded mbarrier wait in clock cycles (the executor's limit unit); the
+// first poll does not block.
+__device__ __forceinline__ bool mbar_wait_cycles(uint64_t* bar, uint32_t parity, long long limit) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (clock64() - t0 <= limit)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// The tiles [t0, t1) of one TMA-staged strided segment, double-buffered in
+// `smem` (which must be 128-byte aligned: a tensor copy's shared-memory end).
+// ph[b] is the phase the next completion of buffer b's barrier will have
+// (the same in every thread).  Returns 0, or the device status bit of the
+// failure (TFFT_DEVICE_ETIMEOUT: a copy wait expired).
+template <int L, int E, int W, int... Rs>
+__device__ int tma_item(const BatchSeg& S, int64_t t0, int64_t t1, float2* smem, int tid, uint64_t* bars,
+                        uint32_t (&ph)[2], long long limit) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  const StridedArgs& a = S.sa;
+  const CUtensorMap* tin = static_cast<const CUtensorMap*>(S.tin);
+  const CUtensorMap* tout = static_cast<const CUtensorMap*>(S.tout);
+  const int tax = a.oax0;
+  const int cx = tid % W, jt = tid / W;
+  const bool inv = a.sign > 0;
+  auto issue_load = [&](int64_t tile, float2* dst, uint64_t* bar) {
+    int64_t o;
+    int2 blk;
+    tile_place(a, tile, o, blk);
+    mbar_expect_tx(bar, (uint32_t)(L * W * sizeof(float2)));
+    for (int k = 0; k < S.gin.nops; ++k) {
+      int c[5];
+      tile_coords(S.gin, a.axis, k, blk.x, o, tax, c);
+      tma_load_5d(dst + (size_t)k * S.gin.rows_per_op * W, tin, bar, c);
+    }
+  };
+  if (tid == 0) {
+    // the previous pass wrote through the generic proxy (plain tiles); this
+    // CTA's earlier tiles used the buffers through it too
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    fence_proxy_async();
+    issue_load(t0, smem, &bars[0]);
+  }
+  int err = 0;
+  for (int64_t tile = t0; tile < t1; ++tile) {
+    const int bi = (int)((tile - t0) & 1);
+    float2* cur = smem + (size_t)bi * L * W;
+    const bool more = tile + 1 < t1;
+    if (tid == 0 && more) {
+      bulk_wait_read<0>();  // the previous tile's store has read the other buffer
+      fence_proxy_async();
+      issue_load(tile + 1, smem + (size_t)(bi ^ 1) * L * W, &bars[bi ^ 1]);
+    }
+    const bool got = mbar_wait_cycles(&bars[bi], ph[bi], limit);
+    ph[bi] ^= 1;
+    if (__syncthreads_or(!got)) {
+      if (tid == 0) {  // let the copies in flight land before the CTA leaves
+        if (!got) mbar_wait(&bars[bi], ph[bi] ^ 1, kWaitLimit);
+        if (more) mbar_wait(&bars[bi ^ 1], ph[bi ^ 1], kWaitLimit);
+      }
+      err = TFFT_DEVICE_ETIMEOUT;
+      break;
+    }
+    float2 v[E];
+    static_for<0, NST>([&](auto St) {
+      constexpr int s = decltype(St)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float2 x = cur[(jt + q * T + r * (L / R)) * W + cx];
+            if (inv) x.y = -x.y;
+            v[q * R + r] = x;
+          }
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / Rp; ++q)
+#pragma unroll
+          for (int r = 0; r < Rp; ++r) cur[stockham_out_index(jt + q * T, Nsp, Rp, r) * W + cx] = v[q * Rp + r];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < E / R; ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = cur[(jt + q * T + r * (L / R)) * W + cx];
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < E / RL; ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        float2 x = cscale(v[q * RL + r], a.scale);
+        if (inv) x.y = -x.y;
+        cur[(jt + q * T + r * (L / RL)) * W + cx] = x;
+      }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      int64_t o;
+      int2 blk;
+      tile_place(a, tile, o, blk);
+      for (int k = 0; k < S.gout.nops; ++k) {
+        int c[5];
+        tile_coords(S.gout, a.axis, k, blk.x, o, tax, c);
+        tma_store_5d(tout, cur + (size_t)k * S.gout.rows_per_op * W, c);
+      }
+      bulk_commit();
+    }
+  }
+  if (tid == 0) bulk_wait_all();  // the item's stores are complete before it is published
+  return err;
+}
 
 template <int KIND, int L, int E, int BW, int... Rs>
 __device__ __forceinline__ void run_tile(const BatchSeg& S, int64_t tile, float2* smem, int tid) {
@@ -52,7 +187,10 @@ __device__ __forceinline__ void run_tile(const BatchSeg& S, int64_t tile, float2
 constexpr int kSmemSegs = 1024;
 
 __global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const BatchArgs b) {
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(128) float2 smem_raw[];
+  // the dynamic block follows the static shared variables: the tile buffers
+  // start at its first 128-byte boundary (batch_smem() adds the slack)
+  float2* smem = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   // the current item's segment, copied out of global memory: read there, its
   // fields would be reloaded after every global store of a tile (the
   // compiler cannot rule out that the store changed them)
@@ -61,10 +199,17 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const BatchArgs b) {
   __shared__ long long s_item;
   __shared__ int s_seg;
   __shared__ int s_abort;
+  __shared__ __align__(8) uint64_t s_bars[2];  // TMA tile buffers 0 and 1
   const int tid = threadIdx.x;
   const bool seg_in_smem = b.nsegs <= kSmemSegs;
   if (seg_in_smem)
     for (int i = tid; i < b.nsegs; i += kBatchThreads) s_first[i] = b.segs[i].first;
+  if (tid == 0) {
+    mbar_init(&s_bars[0], 1);
+    mbar_init(&s_bars[1], 1);
+    fence_mbar_init();
+  }
+  uint32_t ph[2] = {0, 0};
   // items are taken one ahead: the next one is claimed while the current one runs
   long long next = 0;
   if (tid == 0) next = (long long)atomicAdd(b.head, 1ull);
@@ -124,6 +269,28 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const BatchArgs b) {
     // an item is a run of up to `per_item` consecutive tiles of one segment
     const int64_t t0 = (item - S.first) * S.per_item;
     const int64_t t1 = (t0 + S.per_item < S.ntiles) ? t0 + S.per_item : S.ntiles;
+    if (S.tma) {
+      // the tensor copies need a 128-byte aligned shared-memory end
+      int err = (static_cast<uint32_t>(__cvta_generic_to_shared(smem)) & 127) ? TFFT_DEVICE_EALIGN : 0;
+      if (!err) switch (S.variant) {
+#define X(ID, L, E, W, ...)                                                            \
+  case ID:                                                                             \
+    err = tma_item<L, E, W, __VA_ARGS__>(S, t0, t1, smem, tid, s_bars, ph, b.spin_limit); \
+    break;
+          TFFT_BATCH_TMA_VARIANTS(X)
+#undef X
+          default:
+            break;
+        }
+      if (err) {
+        if (tid == 0) {
+          atomicOr(b.status, err);
+          atomicExch(b.abort, 1);
+        }
+        break;
+      }
+      __syncthreads();
+    } else
     for (int64_t tile = t0; tile < t1; ++tile) {
       switch (S.variant) {
 #define X(ID, KIND, L, E, BW, ...)                              \
@@ -153,7 +320,14 @@ constexpr size_t batch_smem() {
   }
   TFFT_BATCH_VARIANTS(X)
 #undef X
-  return m;
+#define X(ID, L, E, W, ...)                                   \
+  {                                                           \
+    const size_t v = 2 * (size_t)L * W * sizeof(float2);      \
+    m = v > m ? v : m;                                        \
+  }
+  TFFT_BATCH_TMA_VARIANTS(X)
+#undef X
+  return m + 128;  // slack to align the tile buffers (see k_batch)
 }
 
 }  // namespace
@@ -182,6 +356,39 @@ bool batch_variant(int id, int& kind, int& L, int& E, int& BW, AxisPlan& ap) {
   }
     TFFT_BATCH_VARIANTS(X)
 #undef X
+#define X(ID, LL, EE, WW, ...)                                          \
+  case ID: {                                                            \
+    const int r[] = {__VA_ARGS__};                                      \
+    kind = 1;                                                           \
+    L = LL;                                                             \
+    E = EE;                                                             \
+    BW = WW;                                                            \
+    ap = AxisPlan{};                                                    \
+    ap.L = LL;                                                          \
+    ap.E = EE;                                                          \
+    ap.T = LL / EE;                                                     \
+    ap.nst = (int)(sizeof(r) / sizeof(int));                            \
+    for (int s = 0; s < ap.nst; ++s) {                                  \
+      ap.radix[s] = r[s];                                               \
+      ap.code |= (uint64_t)r[s] << (5 * s);                             \
+    }                                                                   \
+    ap.spec = 1;                                                        \
+    ap.width = WW;                                                      \
+    return true;                                                        \
+  }
+    TFFT_BATCH_TMA_VARIANTS(X)
+#undef X
+    default:
+      return false;
+  }
+}
+
+bool batch_variant_tma(int id) {
+  switch (id) {
+#define X(ID, ...) case ID:
+    TFFT_BATCH_TMA_VARIANTS(X)
+#undef X
+    return true;
     default:
       return false;
   }
@@ -191,6 +398,7 @@ int batch_num_variants() {
   int n = 0;
 #define X(ID, ...) ++n;
   TFFT_BATCH_VARIANTS(X)
+  TFFT_BATCH_TMA_VARIANTS(X)
 #undef X
   return n;
 }

@@ -1628,7 +1628,7 @@ struct tfft_batch_s {
   std::map<std::pair<int, int>, int> choice;  // (kind, L) -> executor variant
   std::vector<void*> ins, outs, works;
   char* d_state = nullptr;
-  size_t state_bytes = 0, ctr_off = 0, seg_off = 0, cb_off = 0;
+  size_t state_bytes = 0, ctr_off = 0, seg_off = 0, cb_off = 0, map_off = 0;  // map_off: 2 tensor maps per segment
   int64_t nitems = 0;
   long long spin_limit = 4000000000LL;  // clock cycles (~2 s at 2 GHz)
 };
@@ -1658,11 +1658,32 @@ int batch_upload(tfft_batch b, cudaStream_t st) {
     BatchSegH& h = b->segs[i];
     tfft_plan p = b->plans[h.t];
     const Step& s = b->steps[h.t][h.pass];
-    const int v = b->choice[{h.kind, h.L}];
+    int v = b->choice[{h.kind, h.L}];
     int k, l, e, bw;
     AxisPlan ap{};
     batch_variant(v, k, l, e, bw, ap);
     void* bufs[4] = {b->ins[h.t], b->outs[h.t], b->works[h.t], nullptr};
+    // a TMA variant needs equal blocks and aligned columns in both layouts;
+    // other segments of the same length take the first plain variant
+    TmaGeo gin{}, gout{};
+    bool tma = false;
+    if (batch_variant_tma(v)) {
+      tma = p->use_tma && tma_geo(p, s.lin, s.axis, bw, gin) && tma_geo(p, s.lout, s.axis, bw, gout);
+      if (tma) {
+        alignas(64) CUtensorMap maps[2];
+        tma = encode_stage_map(p, gin, s.axis, bw, bufs[s.src], &maps[0]) &&
+              encode_stage_map(p, gout, s.axis, bw, bufs[s.dst], &maps[1]);
+        if (tma) std::memcpy(img.data() + b->map_off + (size_t)i * sizeof(maps), maps, sizeof(maps));
+      }
+      if (!tma) {
+        for (int c : batch_candidates(h.kind, h.L))
+          if (!batch_variant_tma(c)) {
+            v = c;
+            break;
+          }
+        batch_variant(v, k, l, e, bw, ap);
+      }
+    }
     BatchSeg& D = dsegs[i];
     std::memset(&D, 0, sizeof(D));
     D.kind = h.kind;
@@ -1717,6 +1738,13 @@ int batch_upload(tfft_batch b, cudaStream_t st) {
       a.scale = scale;
       a.status = status;
       D.ntiles = nouter * a.ncolblocks;
+      if (tma) {
+        D.tma = 1;
+        D.gin = gin;
+        D.gout = gout;
+        D.tin = b->d_state + b->map_off + (size_t)i * 2 * sizeof(CUtensorMap);
+        D.tout = b->d_state + b->map_off + ((size_t)i * 2 + 1) * sizeof(CUtensorMap);
+      }
     }
     // items of about 32K elements: small tiles are grouped so that the queue,
     // the lookup and the completion fence are paid once per ~512 KB moved
@@ -1813,7 +1841,8 @@ int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int si
   b->ctr_off = 256;
   b->seg_off = b->ctr_off + align_up(16 + b->segs.size() * sizeof(int), 256);
   b->cb_off = b->seg_off + align_up(b->segs.size() * sizeof(BatchSeg), 256);
-  b->state_bytes = b->cb_off + cb_total;
+  b->map_off = b->cb_off + align_up(cb_total, 256);
+  b->state_bytes = b->map_off + b->segs.size() * 2 * sizeof(CUtensorMap);
   b->ins.assign(count, nullptr);
   b->outs.assign(count, nullptr);
   b->works.assign(count, nullptr);
@@ -1846,6 +1875,8 @@ int tfft_batch_bind(tfft_batch b, void* d_state, size_t bytes, const void* const
   if (!b || !ins || !outs) return fail(TFFT_EINVAL, "NULL argument");
   int rc = check_ptr(d_state, "d_state");
   if (rc) return rc;
+  if (reinterpret_cast<uintptr_t>(d_state) & 255)
+    return fail(TFFT_EALIGN, "batch state must be 256-byte aligned (it holds tensor maps)");
   if (bytes < b->state_bytes) return fail(TFFT_EINVAL, "batch state buffer too small");
   const int n = (int)b->plans.size();
   for (int t = 0; t < n; ++t) {
@@ -1942,6 +1973,18 @@ int tfft_batch_autotune(tfft_batch b, int reps, void* stream) {
     }
   }
   return batch_upload(b, st);
+}
+
+int tfft_batch_set_variant(tfft_batch b, int kind, int L, int variant, void* stream) {
+  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+  auto it = b->choice.find({kind, L});
+  if (it == b->choice.end()) return fail(TFFT_EINVAL, "the batch has no pass of that kind and length");
+  const std::vector<int> cands = batch_candidates(kind, L);
+  if (std::find(cands.begin(), cands.end(), variant) == cands.end())
+    return fail(TFFT_EINVAL, "not a compiled variant for that kind and length");
+  it->second = variant;
+  return batch_upload(b, static_cast<cudaStream_t>(stream));
 }
 
 int tfft_batch_set_wait_limit(tfft_batch b, long long cycles) {

@@ -12,6 +12,7 @@ namespace tfft {
 // Bits of the plan's device status word (set by kernels, read by
 // tfft_plan_device_status()).
 constexpr int TFFT_DEVICE_ETIMEOUT = 1;  // a bounded wait on a copy expired
+constexpr int TFFT_DEVICE_EALIGN = 2;    // a TMA tile buffer was not 128-byte aligned (copy skipped)
 
 // Batched 1-D FFT of contiguous lines (the axis held whole and innermost,
 // Eq. pencil0 / slab0): line l of the buffer is elements [l L, (l + 1) L).
@@ -153,6 +154,13 @@ struct BatchSeg {
   int64_t nitems;   // items of the segment = ceil(ntiles / per_item)
   ContigArgs ca;
   StridedArgs sa;
+  // strided tiles staged by TMA (variant of the TMA list): the tile geometry
+  // of the input and output layouts and their tensor maps (CUtensorMap, in
+  // the batch state, 64-byte aligned)
+  int tma;
+  TmaGeo gin, gout;
+  const void* tin;
+  const void* tout;
 };
 
 struct BatchArgs {
@@ -167,6 +175,7 @@ struct BatchArgs {
 };
 
 bool batch_variant(int id, int& kind, int& L, int& E, int& BW, AxisPlan& ap);
+bool batch_variant_tma(int id);  // a TMA-staged strided variant
 int batch_num_variants();
 int batch_grid();
 cudaError_t launch_batch(const BatchArgs& b, int grid, cudaStream_t s);

@@ -351,6 +351,10 @@ class Batch:
         call("tfft_batch_num_items", self._h, ctypes.byref(items), ctypes.byref(segs))
         return items.value, segs.value
 
+    def set_variant(self, kind: int, L: int, variant: int, stream=None):
+        """Choose the executor tile variant of (kind, L) by hand (tfft_batch_set_variant)."""
+        call("tfft_batch_set_variant", self._h, kind, L, variant, _stream_ptr(stream))
+
     def variant(self, kind: int, L: int) -> int:
         v = ctypes.c_int()
         call("tfft_batch_variant", self._h, kind, L, ctypes.byref(v))

@@ -113,3 +113,40 @@ def test_tma_wait_expiry_reports_status(cuda_device):
     assert p.device_status() == 0
     pp = Plan(shape, grid, device=cuda_device, tma=False)
     assert torch.equal(y, pp.forward(x))
+
+
+def test_batch_tma_tiles_match_standalone(cuda_device):
+    """The TMA-staged strided tiles of the executor (variants 15-17: lengths 64, 128, 256),
+    chosen by hand: the same bits as the standalone passes; and their bounded copy waits
+    report an expiry through the status word."""
+    from paper_1804_09536_gb300.plan import Batch
+    from paper_1804_09536_gb300._lib import TfftError
+    plans = _plans(SMALL, cuda_device)
+    b = Batch(plans, sign=-1)
+    for k, (shape, grid) in enumerate(SMALL):
+        b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(shape, seed=200 + k).to(cuda_device), 0))
+    chosen = 0
+    for L, v in ((64, 15), (128, 16), (256, 17)):
+        try:
+            b.set_variant(1, L, v)
+            chosen += 1
+        except TfftError:
+            pass
+    assert chosen == 3
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    refs = [p.forward(b.ins[k]) for k, p in enumerate(plans)]
+    torch.cuda.synchronize()
+    for k in range(len(SMALL)):
+        assert torch.equal(b.outs[k], refs[k]), (k, SMALL[k])
+    b.set_wait_limit(1)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status(reset=True) == 1
+    b.set_wait_limit(0)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    for k in range(len(SMALL)):
+        assert torch.equal(b.outs[k], refs[k]), k
