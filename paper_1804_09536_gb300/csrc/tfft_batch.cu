@@ -50,7 +50,8 @@ using namespace tma;
 #define TFFT_BATCH_TMA_VARIANTS(X) \
   X(15, 64, 8, 32, 8, 8)           \
   X(16, 128, 16, 32, 16, 8)        \
-  X(17, 256, 16, 16, 16, 16)
+  X(17, 256, 16, 16, 16, 16)       \
+  X(18, 96, 12, 32, 4, 4, 3, 2)
 
 constexpr int kBatchThreads = 256;
 

@@ -1635,14 +1635,20 @@ struct tfft_batch_s {
 
 namespace {
 
+// Executor variants for passes of (kind, L); the first is the default
+// before autotuning: TMA-staged strided variants lead (measured faster on
+// the 48-transform batch, and a segment that cannot use them falls back to
+// the first plain variant by itself).
 std::vector<int> batch_candidates(int kind, int L) {
-  std::vector<int> v;
+  std::vector<int> tma, plain;
   for (int id = 0; id < batch_num_variants(); ++id) {
     int k, l, e, bw;
     AxisPlan ap{};
-    if (batch_variant(id, k, l, e, bw, ap) && k == kind && l == L) v.push_back(id);
+    if (batch_variant(id, k, l, e, bw, ap) && k == kind && l == L)
+      (batch_variant_tma(id) ? tma : plain).push_back(id);
   }
-  return v;
+  tma.insert(tma.end(), plain.begin(), plain.end());
+  return tma;
 }
 
 

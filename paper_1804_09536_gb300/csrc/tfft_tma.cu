@@ -198,7 +198,9 @@ cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo
 // another (autotuning).
 #define TFFT_TMA_STRIDED(X)     \
   X(64, 8, 32, 8, 8)            \
+  X(96, 12, 32, 4, 4, 3, 2)     \
   X(128, 16, 32, 16, 8)         \
+  X(160, 20, 16, 5, 4, 4, 2)    \
   X(256, 16, 32, 16, 16)        \
   X(512, 32, 16, 32, 16)        \
   X(512, 16, 16, 8, 8, 8)

@@ -116,7 +116,7 @@ def test_tma_wait_expiry_reports_status(cuda_device):
 
 
 def test_batch_tma_tiles_match_standalone(cuda_device):
-    """The TMA-staged strided tiles of the executor (variants 15-17: lengths 64, 128, 256),
+    """The TMA-staged strided tiles of the executor (variants 15-18: lengths 64, 128, 256, 96),
     chosen by hand: the same bits as the standalone passes; and their bounded copy waits
     report an expiry through the status word."""
     from paper_1804_09536_gb300.plan import Batch
@@ -126,13 +126,13 @@ def test_batch_tma_tiles_match_standalone(cuda_device):
     for k, (shape, grid) in enumerate(SMALL):
         b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(shape, seed=200 + k).to(cuda_device), 0))
     chosen = 0
-    for L, v in ((64, 15), (128, 16), (256, 17)):
+    for L, v in ((64, 15), (128, 16), (256, 17), (96, 18)):
         try:
             b.set_variant(1, L, v)
             chosen += 1
         except TfftError:
             pass
-    assert chosen == 3
+    assert chosen == 4
     b.execute()
     torch.cuda.synchronize()
     assert b.device_status() == 0

@@ -31,7 +31,8 @@ CASES = [
     ((128,), ()),                    # 1-D, no grid
     ((1, 16, 8), (1, 2)),            # length-1 axis
     ((256, 128, 256), (2, 4)),       # TMA-staged passes (equal blocks, lengths 128/256)
-    ((512, 64, 64), (4, 2)),         # TMA-staged passes, 512-row boxes split in two
+    ((512, 64, 64), (4, 2)),         # TMA-staged passes, a 512-row axis split in two tensor dimensions
+    ((96, 160, 64), (2, 2)),         # TMA-staged passes of lengths 96 and 160
     ((42, 127, 256), (3, 4)),        # the paper's App. A shape: 42 = 2.3.7 and 127 (prime) by Bluestein
     ((7, 11, 26), (2, 3)),           # Bluestein on every axis (26 = 2.13), uneven blocks
     ((2047,), ()),                   # the longest Bluestein line (convolution length 4096)
