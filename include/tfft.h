@@ -38,8 +38,9 @@
  * the caller; the plan itself is a host object.  Every device pointer must be
  * 16-byte aligned.  Calls are asynchronous on the given stream (a
  * cudaStream_t passed as void*; NULL is the legacy default stream) and do not
- * synchronise, except tfft_plan_bind(), which is a set-up call and returns
- * after its copies are complete.
+ * synchronise, except the set-up calls tfft_plan_bind(), tfft_batch_bind(),
+ * tfft_batch_autotune() and tfft_batch_set_variant(), which return after
+ * their copies (and, for the autotuner, its timed runs) are complete.
  *
  * Errors: every call returns a tfft_status.  Arguments are validated before
  * anything is launched; on an error nothing is launched and
@@ -84,7 +85,7 @@ enum {
 typedef enum {
   TFFT_OK = 0,
   TFFT_EINVAL = 1,       /* bad argument (shape, grid, axis, stage, sign, pointer) */
-  TFFT_EUNSUPPORTED = 2, /* valid request this build does not implement (e.g. a prime length) */
+  TFFT_EUNSUPPORTED = 2, /* valid request this build does not implement (e.g. a prime length > 2048) */
   TFFT_EALIGN = 3,       /* a device pointer is not 16-byte aligned */
   TFFT_EWORKSPACE = 4,   /* workspace missing or too small */
   TFFT_ECUDA = 5,        /* a CUDA runtime call failed */
