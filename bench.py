@@ -262,6 +262,10 @@ def run_ours(args):
     r2c = r2c_slab(plan_cls=Plan, dev=dev, steps=max(5, min(args.steps, 50)), barrier=barrier,
                    tma=not args.no_tma)
 
+    # r2c on pencils (the paper's own benchmark kind): 512^3 real on 4 x 8
+    r2c_p = r2c_slab(plan_cls=Plan, dev=dev, steps=max(3, min(args.steps, 20)), barrier=barrier,
+                     tma=not args.no_tma, shape=(512, 512, 512), grid=(4, 8))
+
     # the 4-D case: 128^4 on a 3-D virtual grid
     fd = fourd_128(plan_cls=Plan, dev=dev, steps=max(3, min(args.steps, 20)), barrier=barrier,
                    tma=not args.no_tma)
@@ -334,6 +338,7 @@ def run_ours(args):
                                    "packed": round(extra["packed"], 4)},
         "fused_vs_packed_speedup": round(extra["packed"] / ms_step, 3),
         "r2c_slab_256": r2c,
+        "r2c_pencil_512": r2c_p,
         "fourd_128": fd,
         "tensor_core_512": tc,
         "autograd_512": ag,
@@ -391,16 +396,15 @@ def profile_workload(args, dev):
                       "ms_per_step": a.elapsed_time(e) / args.steps}))
 
 
-def r2c_slab(plan_cls, dev, steps, barrier, tma=True):
-    """256^3 real-to-complex (output 256 x 256 x 129) on a virtual 8-rank slab,
-    forward + inverse, fused and packed; ms per step and the HBM fraction of
-    the fused path's algorithmic bytes."""
+def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), grid=(8,)):
+    """Real-to-complex forward + inverse on a virtual grid (default: 256^3 on an
+    8-rank slab, output 256 x 256 x 129), fused and packed; ms per step and the
+    HBM fraction of the fused path's algorithmic bytes."""
     import torch
     from paper_1804_09536_gb300 import inputs
-    shape, grid = (256, 256, 256), (8,)
     p = plan_cls(shape, grid, kind="r2c", device=dev, tma=tma)
     x = p.scatter(inputs.normal_real(shape, seed=0).to(dev), 0, real=True)
-    y = p.empty_stage(1)
+    y = p.empty_stage(p.g)
     z = p.empty_stage(0, real=True)
     out = {}
     nbytes = 0
@@ -425,7 +429,9 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True):
             nbytes = sum(n for _, n in p.launch_info(-1, mode) + p.launch_info(+1, mode))
     peak, _ = _peaks()
     n = math.prod(shape)
-    return {"workload": "256x256x256 r2c float32 -> 256x256x129 complex64, virtual slab 8, forward+inverse",
+    oshape = "x".join(str(v) for v in shape[:-1] + (shape[-1] // 2 + 1,))
+    return {"workload": f"{'x'.join(map(str, shape))} r2c float32 -> {oshape} complex64, virtual grid "
+                        f"{'x'.join(map(str, grid))}, forward+inverse",
             "fused_ms": round(out["fused"], 4), "packed_ms": round(out["packed"], 4),
             "fused_vs_packed_speedup": round(out["packed"] / out["fused"], 3),
             "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),

@@ -302,3 +302,26 @@ def test_full_size_r2c_256_slab_sampled(cuda_device):
     assert abs(e_out - e_in) <= 1e-5 * e_in
     back = p.inverse(y.clone())
     assert float(torch.linalg.vector_norm((back - b0).double()) / torch.linalg.vector_norm(b0.double())) <= RTOL_FP32
+
+
+@pytest.mark.slow
+def test_full_size_r2c_512_pencil_sampled(cuda_device):
+    """r2c on a pencil grid at the size bench.py measures (512^3 real on 4 x 8): sampled
+    outputs of the Hermitian half against the oracle's definition and the c2r round trip."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (512, 512, 512), (4, 8)
+    x = inputs.normal_real(shape, seed=0)
+    p = Plan(shape, grid, kind="r2c", device=cuda_device)
+    b0 = p.scatter(x.to(cuda_device), 0, real=True)
+    y = p.forward(b0)
+    yg = p.gather(y, 2).cpu().numpy()
+    assert yg.shape == (512, 512, 257)
+    rng = np.random.default_rng(4)
+    ks = [(0, 0, 0), (511, 511, 256), (3, 2, 1)] + [
+        (int(rng.integers(0, 512)), int(rng.integers(0, 512)), int(rng.integers(0, 257))) for _ in range(3)]
+    want = dft.forward_at(x.numpy().astype(np.complex64), ks, chunk=16)
+    got = np.array([yg[k] for k in ks])
+    rms = float(np.sqrt(np.mean(np.abs(yg.astype(np.complex128)) ** 2)))
+    assert np.max(np.abs(got - want)) <= 1e-4 * rms
+    back = p.inverse(y.clone())
+    assert float(torch.linalg.vector_norm((back - b0).double()) / torch.linalg.vector_norm(b0.double())) <= RTOL_FP32
