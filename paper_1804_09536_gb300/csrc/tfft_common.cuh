@@ -56,26 +56,6 @@ TFFT_HD void locate(int64_t N64, int64_t M64, int64_t g64, int64_t& coord, int64
   }
 }
 
-// Element offset of global index (g0, g1, g2, g3) (only the first d used).
-TFFT_HD int64_t layout_addr(const DevLayout& L, int64_t g0, int64_t g1, int64_t g2,
-                            int64_t g3) {
-  const int64_t gi[MAXD] = {g0, g1, g2, g3};
-  int64_t rank = 0, lin = 0;
-#pragma unroll
-  for (int m = 0; m < MAXD; ++m) {
-    if (m < L.d) {
-      int64_t local = gi[m], n = L.N[m];
-      if (L.Mx[m] > 1) {
-        int64_t coord;
-        locate(L.N[m], L.Mx[m], gi[m], coord, local, n);
-        rank += coord * L.rs[m];
-      }
-      lin = lin * n + local;
-    }
-  }
-  return L.offset[rank] + lin;
-}
-
 // ------------------------------------------------------------ complex math
 
 TFFT_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

@@ -94,6 +94,67 @@ struct StridedArgs {
   uint32_t wait_limit;    // polls of a bounded copy wait (TMA passes)
 };
 
+#ifdef __CUDACC__
+// Outer index (split into the two outer axes' indices) and column block of
+// strided tile `tile`.
+struct StridedTilePos {
+  int64_t go0, go1;
+  int2 blk;
+  __device__ __forceinline__ StridedTilePos(const StridedArgs& a, int64_t tile) {
+    const int64_t o = tile / a.ncolblocks;
+    blk = a.colblocks[tile - o * a.ncolblocks];
+    go0 = (a.oax1 >= 0) ? o / a.on1 : o;
+    go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+  }
+};
+
+// The rows of one strided tile in one layout, with everything that does not
+// depend on the row folded once per tile: the fixed axes' rank part and, in
+// the C-order index of a rank's local array, the part before the FFT axis
+// (head, scaled by that axis' local extent n_a, which depends on the row's
+// part when the split is uneven) and after it (tail, with stride prod).
+// Row i is then one locate() along the FFT axis: rank = base + c_a rs_a,
+// index = (head n_a + l_a) prod + tail; the element offset is the rank's
+// offset plus that index.
+struct TileRows {
+  int64_t base, head, prod, tail;
+  int64_t N, M, rs;  // the FFT axis in this layout
+  __device__ __forceinline__ TileRows(const StridedArgs& a, const DevLayout& lay, const StridedTilePos& tp) {
+    base = 0;
+    head = 0;
+    prod = 1;
+    tail = 0;
+    N = lay.N[a.axis];
+    M = lay.Mx[a.axis];
+    rs = lay.rs[a.axis];
+#pragma unroll
+    for (int m = 0; m < MAXD; ++m) {
+      if (m >= lay.d || m == a.axis) continue;
+      const int64_t g = (m == a.d - 1) ? (int64_t)tp.blk.x : (m == a.oax0) ? tp.go0 : (m == a.oax1) ? tp.go1 : 0;
+      int64_t local = g, n = lay.N[m];
+      if (lay.Mx[m] > 1) {
+        int64_t c;
+        locate(lay.N[m], lay.Mx[m], g, c, local, n);
+        base += c * lay.rs[m];
+      }
+      if (m < a.axis) {
+        head = head * n + local;
+      } else {
+        tail = tail * n + local;
+        prod *= n;
+      }
+    }
+  }
+  __device__ __forceinline__ int64_t row(const DevLayout& lay, int i) const {
+    int64_t c = 0, l = i, n = N;
+    if (M > 1) locate(N, M, i, c, l, n);
+    return lay.offset[base + c * rs] + (head * n + l) * prod + tail;
+  }
+};
+
+#endif
+
+
 // Tile geometry of one stage layout seen as the 5-D array
 // [rank dim 4][rank dim 3][n0][n1][n2] (d = 3, equal blocks on every rank):
 // for each axis m, whether it is cut, its local extent and the 5-D dimension

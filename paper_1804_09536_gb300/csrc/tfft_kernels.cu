@@ -149,22 +149,13 @@ __global__ void __launch_bounds__(512, 1) k_fft_strided(const StridedArgs a) {
   const bool inv = a.sign > 0;
   const int64_t ntiles = a.nouter * a.ncolblocks;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t o = tile / a.ncolblocks;
-    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
-    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
-    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    const StridedTilePos tp(a, tile);
+    const int2 blk = tp.blk;
+    const TileRows ri(a, a.lin, tp), ro(a, a.lout, tp);
     __syncthreads();  // the previous tile is done with the row tables
     for (int i = tid; i < L; i += nthr) {
-      int64_t g[MAXD];
-#pragma unroll
-      for (int m = 0; m < MAXD; ++m)
-        g[m] = (m == a.axis) ? (int64_t)i
-             : (m == a.d - 1) ? (int64_t)blk.x
-             : (m == a.oax0) ? go0
-             : (m == a.oax1) ? go1
-                             : 0;
-      rin[i] = layout_addr(a.lin, g[0], g[1], g[2], g[3]);
-      rout[i] = layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+      rin[i] = ri.row(a.lin, i);
+      rout[i] = ro.row(a.lout, i);
     }
     __syncthreads();
     const bool act = cx < blk.y;
@@ -324,22 +315,13 @@ __global__ void __launch_bounds__(512) k_fft_strided_generic(const StridedArgs a
   const bool inv = a.sign > 0;
   const int64_t ntiles = a.nouter * a.ncolblocks;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t o = tile / a.ncolblocks;
-    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
-    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
-    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    const StridedTilePos tp(a, tile);
+    const int2 blk = tp.blk;
+    const TileRows ri(a, a.lin, tp), ro(a, a.lout, tp);
     __syncthreads();
     for (int i = tid; i < L; i += nthr) {
-      int64_t g[MAXD];
-#pragma unroll
-      for (int m = 0; m < MAXD; ++m)
-        g[m] = (m == a.axis) ? (int64_t)i
-             : (m == a.d - 1) ? (int64_t)blk.x
-             : (m == a.oax0) ? go0
-             : (m == a.oax1) ? go1
-                             : 0;
-      rin[i] = layout_addr(a.lin, g[0], g[1], g[2], g[3]);
-      rout[i] = layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+      rin[i] = ri.row(a.lin, i);
+      rout[i] = ro.row(a.lout, i);
     }
     __syncthreads();
     for (int idx = tid; idx < L * W; idx += nthr) {
@@ -423,22 +405,13 @@ __global__ void __launch_bounds__(512) k_blue_strided(const StridedArgs a, const
   const bool inv = a.sign > 0;
   const int64_t ntiles = a.nouter * a.ncolblocks;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t o = tile / a.ncolblocks;
-    const int2 blk = a.colblocks[tile - o * a.ncolblocks];
-    const int64_t go0 = (a.oax1 >= 0) ? o / a.on1 : o;
-    const int64_t go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+    const StridedTilePos tp(a, tile);
+    const int2 blk = tp.blk;
+    const TileRows ri(a, a.lin, tp), ro(a, a.lout, tp);
     __syncthreads();
     for (int i = tid; i < N; i += nthr) {
-      int64_t g[MAXD];
-#pragma unroll
-      for (int m = 0; m < MAXD; ++m)
-        g[m] = (m == a.axis) ? (int64_t)i
-             : (m == a.d - 1) ? (int64_t)blk.x
-             : (m == a.oax0) ? go0
-             : (m == a.oax1) ? go1
-                             : 0;
-      rin[i] = layout_addr(a.lin, g[0], g[1], g[2], g[3]);
-      rout[i] = layout_addr(a.lout, g[0], g[1], g[2], g[3]);
+      rin[i] = ri.row(a.lin, i);
+      rout[i] = ro.row(a.lout, i);
     }
     __syncthreads();
     for (int idx = tid; idx < M * W; idx += nthr) {

@@ -223,30 +223,6 @@ __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, f
 
 // ------------------------------------------------------------ strided lines
 
-// Outer index and column block of strided tile `tile`, and the element
-// offset of its row i (position i along the FFT axis) in a stage layout.
-struct StridedTilePos {
-  int64_t go0, go1;
-  int2 blk;
-  __device__ __forceinline__ StridedTilePos(const StridedArgs& a, int64_t tile) {
-    const int64_t o = tile / a.ncolblocks;
-    blk = a.colblocks[tile - o * a.ncolblocks];
-    go0 = (a.oax1 >= 0) ? o / a.on1 : o;
-    go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
-  }
-  __device__ __forceinline__ int64_t row(const StridedArgs& a, const DevLayout& lay, int i) const {
-    int64_t g[MAXD];
-#pragma unroll
-    for (int m = 0; m < MAXD; ++m)
-      g[m] = (m == a.axis) ? (int64_t)i
-           : (m == a.d - 1) ? (int64_t)blk.x
-           : (m == a.oax0) ? go0
-           : (m == a.oax1) ? go1
-                           : 0;
-    return layout_addr(lay, g[0], g[1], g[2], g[3]);
-  }
-};
-
 // One strided tile (outer index and column block `tile`): thread jt of
 // column cx; tid = thread index in the CTA (W x T threads).
 template <int L, int E, int W, bool CG, int... Rs>
@@ -257,10 +233,11 @@ __device__ __forceinline__ void strided_tile(const StridedArgs& a, int64_t tile,
   int* rout = rin + L;
   const bool inv = a.sign > 0;
   const StridedTilePos tp(a, tile);
+  const TileRows ri(a, a.lin, tp), ro(a, a.lout, tp);
   __syncthreads();  // the previous tile is done with the row tables
   for (int i = tid; i < L; i += W * T) {
-    rin[i] = (int)tp.row(a, a.lin, i);
-    rout[i] = (int)tp.row(a, a.lout, i);
+    rin[i] = (int)ri.row(a.lin, i);
+    rout[i] = (int)ro.row(a.lout, i);
   }
   __syncthreads();
   const int2 blk = tp.blk;
