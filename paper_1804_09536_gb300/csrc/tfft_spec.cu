@@ -59,38 +59,42 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     const float2* src = reinterpret_cast<const float2*>(a.rin) + line * L;
     float2* dst = a.cout + line * (L + 1);
     const int jt = opaque_tid_x();
-    float2 v[E];
+    float2 v[emax<L, E, Rs...>()];
     static_for<0, NST>([&](auto S) {
       constexpr int s = decltype(S)::value;
       constexpr int R = radix_at<s, Rs...>();
       constexpr int Ns = span_at<s, Rs...>();
       if constexpr (s == 0) {
 #pragma unroll
-        for (int q = 0; q < E / R; ++q)
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = act ? src[jt + q * T + r * (L / R)] : make_float2(0.f, 0.f);
+          for (int r = 0; r < R; ++r)
+            v[q * R + r] = (act && bf_exists<L, E, R>(jt, q)) ? src[jt + q * T + r * (L / R)] : make_float2(0.f, 0.f);
       } else {
         constexpr int Rp = radix_at<s - 1, Rs...>();
         constexpr int Nsp = Ns / Rp;
         line_sync<T>();
 #pragma unroll
-        for (int q = 0; q < E / Rp; ++q)
+        for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+          if (bf_exists<L, E, Rp>(jt, q))
 #pragma unroll
-          for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+            for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
         line_sync<T>();
 #pragma unroll
-        for (int q = 0; q < E / R; ++q)
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
+          if (bf_exists<L, E, R>(jt, q))
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
+            for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
       }
       spec_stage<L, E, R, Ns>(v, jt, a.tw);
     });
     constexpr int RL = radix_at<NST - 1, Rs...>();
     line_sync<T>();
 #pragma unroll
-    for (int q = 0; q < E / RL; ++q)
+    for (int q = 0; q < nbf<L, E, RL>(); ++q)
+      if (bf_exists<L, E, RL>(jt, q))
 #pragma unroll
-      for (int r = 0; r < RL; ++r) sl[padp<P>(jt + q * T + r * (L / RL))] = v[q * RL + r];
+        for (int r = 0; r < RL; ++r) sl[padp<P>(jt + q * T + r * (L / RL))] = v[q * RL + r];
     line_sync<T>();
     for (int k = jt; k <= L; k += T) {
       const float2 zk = sl[padp<P>(k == L ? 0 : k)];
@@ -138,17 +142,17 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
       }
     }
     line_sync<T>();
-    float2 v[E];
+    float2 v[emax<L, E, Rs...>()];
     static_for<0, NST>([&](auto S) {
       constexpr int s = decltype(S)::value;
       constexpr int R = radix_at<s, Rs...>();
       constexpr int Ns = span_at<s, Rs...>();
       if constexpr (s == 0) {
 #pragma unroll
-        for (int q = 0; q < E / R; ++q)
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const int k = jt + q * T + r * (L / R);
+            const int k = bf_exists<L, E, R>(jt, q) ? jt + q * T + r * (L / R) : 0;
             const float2 xk = sl[padp<P>(k)];
             const float2 xm = sl[padp<P>(L - k)];
             const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);      // X[k] + conj X[L-k]
@@ -163,24 +167,26 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
         constexpr int Nsp = Ns / Rp;
         line_sync<T>();
 #pragma unroll
-        for (int q = 0; q < E / Rp; ++q)
+        for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+          if (bf_exists<L, E, Rp>(jt, q))
 #pragma unroll
-          for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+            for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
         line_sync<T>();
 #pragma unroll
-        for (int q = 0; q < E / R; ++q)
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
+          if (bf_exists<L, E, R>(jt, q))
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
+            for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
       }
       spec_stage<L, E, R, Ns>(v, jt, a.tw);
     });
     constexpr int RL = radix_at<NST - 1, Rs...>();
 #pragma unroll
-    for (int q = 0; q < E / RL; ++q)
+    for (int q = 0; q < nbf<L, E, RL>(); ++q)
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
         const float2 z = v[q * RL + r];
-        if (act) dst[jt + q * T + r * (L / RL)] = make_float2(z.x * a.scale, -z.y * a.scale);
+        if (act && bf_exists<L, E, RL>(jt, q)) dst[jt + q * T + r * (L / RL)] = make_float2(z.x * a.scale, -z.y * a.scale);
       }
   }
 }
@@ -219,7 +225,9 @@ cudaError_t run_strided(const StridedArgs& a, cudaStream_t s) {
 
 // The table of specialisations: length; contiguous passes: elements per
 // thread and lines per CTA; strided passes: elements per thread and tile
-// width; radices.
+// width; radices.  "Elements per thread" is L / (threads per line); for the
+// lengths with 2, 3 and 5 all present no radix set divides it, and the
+// threads carry ceil(butterflies / threads) butterflies per stage (nbf()).
 #define TFFT_SPECS(X)                       \
   X(32, 8, 64, 8, 32, 8, 4)                 \
   X(64, 8, 32, 8, 32, 8, 8)                 \
@@ -227,7 +235,11 @@ cudaError_t run_strided(const StridedArgs& a, cudaStream_t s) {
   X(128, 16, 32, 16, 32, 16, 8)             \
   X(160, 20, 32, 20, 32, 5, 4, 4, 2)        \
   X(256, 16, 16, 16, 32, 16, 16)            \
-  X(512, 32, 16, 32, 16, 32, 16)
+  X(512, 32, 16, 32, 16, 32, 16)            \
+  X(60, 15, 64, 15, 64, 4, 5, 3)            \
+  X(120, 15, 32, 15, 32, 8, 5, 3)           \
+  X(240, 15, 16, 15, 16, 16, 5, 3)          \
+  X(480, 30, 16, 30, 16, 16, 5, 3, 2)
 
 struct SpecRow {
   int L, EC, B, ES, W, nst, radix[6];

@@ -34,12 +34,47 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
+// A line of length L has T = L / E threads.  A stage of radix R has L / R
+// butterflies, nbf = ceil((L / R) / T) per thread: butterfly j = jt + q T,
+// q < nbf, exists when j < L / R.  When every radix divides E this is E / R
+// butterflies each and no guard (the usual plans); lengths with 2, 3 and 5
+// all present (60, 120, 240, 480) have no such E, so their threads carry one
+// butterfly fewer in some stages and hold up to emax() values.
+template <int L, int E, int R>
+__host__ __device__ constexpr int nbf() {
+  return (L / R + L / E - 1) / (L / E);
+}
+
+template <int L, int E, int R>
+__host__ __device__ constexpr bool nbf_exact() {
+  return (L / R) % (L / E) == 0;
+}
+
+template <int L, int E, int... Rs>
+__host__ __device__ constexpr int emax() {
+  constexpr int r[] = {Rs...};
+  int m = 0;
+  for (int i = 0; i < (int)sizeof...(Rs); ++i) {
+    const int v = ((L / r[i] + L / E - 1) / (L / E)) * r[i];
+    m = v > m ? v : m;
+  }
+  return m;
+}
+
+// Whether butterfly q of thread jt exists in a stage of radix R.
+template <int L, int E, int R>
+__device__ __forceinline__ bool bf_exists(int jt, int q) {
+  if constexpr (nbf_exact<L, E, R>()) return true;
+  else return jt + q * (L / E) < L / R;
+}
+
 // Twiddle (stage span Ns > 1) and size-R butterflies of a thread's work items.
-template <int L, int E, int R, int Ns>
-__device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2* __restrict__ tw) {
+template <int L, int E, int R, int Ns, int EM>
+__device__ __forceinline__ void spec_stage(float2 (&v)[EM], int jt, const float2* __restrict__ tw) {
   constexpr int T = L / E;
 #pragma unroll
-  for (int q = 0; q < E / R; ++q) {
+  for (int q = 0; q < nbf<L, E, R>(); ++q) {
+    if (!bf_exists<L, E, R>(jt, q)) continue;
     if constexpr (Ns > 1) {
       const int j = jt + q * T;
       const int step = (j % Ns) * (L / (Ns * R));
@@ -57,6 +92,7 @@ __device__ __forceinline__ void spec_stage(float2 (&v)[E], int jt, const float2*
 // j = jt + q T; the values are stored from offset(s) on, (R - 1) per q.
 template <int L, int E, int... Rs>
 struct StageTwiddles {
+  static_assert(((E % Rs == 0) && ...), "every radix divides E (uniform plans)");
   static constexpr int NST = sizeof...(Rs);
   __host__ __device__ static constexpr int offset(int s) {
     constexpr int r[] = {Rs...};
@@ -117,7 +153,7 @@ __device__ __forceinline__ int opaque_tid_y() {
 // (half that for the 20-element plans, whose butterflies need more registers).
 __host__ __device__ constexpr int min_blocks(int E, int threads, int target) {
   const int t = (E >= 20 ? target / 2 : target) / threads;
-  return t > 1 ? t : (E >= 32 && threads <= 256 ? 2 : 1);
+  return t > 1 ? t : (E >= 30 && threads <= 256 ? 2 : 1);
 }
 
 // Synchronises the threads of one line: a warp (or part of one) when a line
@@ -177,17 +213,18 @@ __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, f
   const bool act = line < a.nlines;
   const float2* src = a.in + line * L;
   float2* dst = a.out + line * L;
-  float2 v[E];
+  float2 v[emax<L, E, Rs...>()];
   static_for<0, NST>([&](auto S) {
     constexpr int s = decltype(S)::value;
     constexpr int R = radix_at<s, Rs...>();
     constexpr int Ns = span_at<s, Rs...>();
     if constexpr (s == 0) {
 #pragma unroll
-      for (int q = 0; q < E / R; ++q)
+      for (int q = 0; q < nbf<L, E, R>(); ++q)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          float2 x = act ? ld<CG>(src + jt + q * T + r * (L / R)) : make_float2(0.f, 0.f);
+          float2 x = (act && bf_exists<L, E, R>(jt, q)) ? ld<CG>(src + jt + q * T + r * (L / R))
+                                                        : make_float2(0.f, 0.f);
           if (inv) x.y = -x.y;
           v[q * R + r] = x;
         }
@@ -196,26 +233,28 @@ __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, f
       constexpr int Nsp = Ns / Rp;
       line_sync<T>();
 #pragma unroll
-      for (int q = 0; q < E / Rp; ++q)
+      for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+        if (bf_exists<L, E, Rp>(jt, q))
 #pragma unroll
-        for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+          for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
       line_sync<T>();
 #pragma unroll
-      for (int q = 0; q < E / R; ++q)
+      for (int q = 0; q < nbf<L, E, R>(); ++q)
+        if (bf_exists<L, E, R>(jt, q))
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
+          for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
     }
     spec_stage<L, E, R, Ns>(v, jt, a.tw);
   });
   constexpr int RL = radix_at<NST - 1, Rs...>();
   const float oscale = contig_scale(a);
 #pragma unroll
-  for (int q = 0; q < E / RL; ++q)
+  for (int q = 0; q < nbf<L, E, RL>(); ++q)
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       float2 x = cscale(v[q * RL + r], oscale);
       if (inv) x.y = -x.y;
-      if (act) dst[jt + q * T + r * (L / RL)] = x;
+      if (act && bf_exists<L, E, RL>(jt, q)) dst[jt + q * T + r * (L / RL)] = x;
     }
   line_sync<T>();  // the line's shared slots are free for the next group
 }
@@ -242,18 +281,18 @@ __device__ __forceinline__ void strided_tile(const StridedArgs& a, int64_t tile,
   __syncthreads();
   const int2 blk = tp.blk;
   const bool act = cx < blk.y;
-  float2 v[E];
+  float2 v[emax<L, E, Rs...>()];
   static_for<0, NST>([&](auto S) {
     constexpr int s = decltype(S)::value;
     constexpr int R = radix_at<s, Rs...>();
     constexpr int Ns = span_at<s, Rs...>();
     if constexpr (s == 0) {
 #pragma unroll
-      for (int q = 0; q < E / R; ++q)
+      for (int q = 0; q < nbf<L, E, R>(); ++q)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int pos = jt + q * T + r * (L / R);
-          float2 x = act ? ld<CG>(a.in + rin[pos] + cx) : make_float2(0.f, 0.f);
+          float2 x = (act && bf_exists<L, E, R>(jt, q)) ? ld<CG>(a.in + rin[pos] + cx) : make_float2(0.f, 0.f);
           if (inv) x.y = -x.y;
           v[q * R + r] = x;
         }
@@ -262,26 +301,28 @@ __device__ __forceinline__ void strided_tile(const StridedArgs& a, int64_t tile,
       constexpr int Nsp = Ns / Rp;
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < E / Rp; ++q)
+      for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+        if (bf_exists<L, E, Rp>(jt, q))
 #pragma unroll
-        for (int r = 0; r < Rp; ++r)
-          smem[stockham_out_index(jt + q * T, Nsp, Rp, r) * W + cx] = v[q * Rp + r];
+          for (int r = 0; r < Rp; ++r)
+            smem[stockham_out_index(jt + q * T, Nsp, Rp, r) * W + cx] = v[q * Rp + r];
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < E / R; ++q)
+      for (int q = 0; q < nbf<L, E, R>(); ++q)
+        if (bf_exists<L, E, R>(jt, q))
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[q * R + r] = smem[(jt + q * T + r * (L / R)) * W + cx];
+          for (int r = 0; r < R; ++r) v[q * R + r] = smem[(jt + q * T + r * (L / R)) * W + cx];
     }
     spec_stage<L, E, R, Ns>(v, jt, a.tw);
   });
   constexpr int RL = radix_at<NST - 1, Rs...>();
 #pragma unroll
-  for (int q = 0; q < E / RL; ++q)
+  for (int q = 0; q < nbf<L, E, RL>(); ++q)
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       float2 x = cscale(v[q * RL + r], a.scale);
       if (inv) x.y = -x.y;
-      if (act) a.out[rout[jt + q * T + r * (L / RL)] + cx] = x;
+      if (act && bf_exists<L, E, RL>(jt, q)) a.out[rout[jt + q * T + r * (L / RL)] + cx] = x;
     }
 }
 

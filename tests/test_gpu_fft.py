@@ -33,6 +33,8 @@ CASES = [
     ((256, 128, 256), (2, 4)),       # TMA-staged passes (equal blocks, lengths 128/256)
     ((512, 64, 64), (4, 2)),         # TMA-staged passes, a 512-row axis split in two tensor dimensions
     ((96, 160, 64), (2, 2)),         # TMA-staged passes of lengths 96 and 160
+    ((60, 120, 240), (2, 4)),        # 2.3.5 lengths: threads with uneven butterfly counts
+    ((480, 60, 120), (3, 2)),
     ((42, 127, 256), (3, 4)),        # the paper's App. A shape: 42 = 2.3.7 and 127 (prime) by Bluestein
     ((7, 11, 26), (2, 3)),           # Bluestein on every axis (26 = 2.13), uneven blocks
     ((2047,), ()),                   # the longest Bluestein line (convolution length 4096)
@@ -216,6 +218,7 @@ def test_full_size_128_4d_sampled(cuda_device):
 
 
 R2C_CASES = [
+    ((8, 12, 480), (2, 2)),          # half-length 240 (2.3.5)
     ((32, 64, 256), (8,)),           # the r2c slab workload's innermost length, 8 ranks
     ((16, 32, 64), (2, 2)),          # r2c on a pencil grid
     ((12, 10, 128), (3,)),           # uneven slab
