@@ -1,0 +1,212 @@
+// Compile-time specialised real-line passes (r2c / c2r along the innermost
+// axis) for the lengths of tfft_spec_table.h (the complex half-length).
+#include "tfft_internal.h"
+#include "tfft_spec_table.h"
+#include "tfft_tiles.cuh"
+
+namespace tfft {
+
+namespace {
+
+using namespace tiles;
+
+// ------------------------------------------------------------ real lines
+//
+// Real-to-complex along the innermost axis (footnote to Eq. multifft: the
+// Hermitian half k = 0 .. N/2).  A real line of N = 2L values is read as L
+// complex values z[n] = x[2n] + i x[2n+1]; Z = FFT_L(z); then with
+// w = exp(-2 pi i / N):  X[k] = (Z[k] + conj Z[L-k]) / 2
+//                              - (i / 2) w^k (Z[k] - conj Z[L-k]),  k = 0 .. L.
+// Complex-to-real inverts it: Z[k] = (X[k] + conj X[L-k])
+//                              + i w^-k (X[k] - conj X[L-k]),  k < L,
+// z = backward FFT_L(Z), x[2n] = Re z[n], x[2n+1] = Im z[n]; the imaginary
+// parts of X[0] and X[L] are ignored (taken as zero).
+
+template <int L, int E, int B, int... Rs>
+__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
+    k_r2c_spec(const RealArgs a) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  constexpr int LP = line_pitch<L, Rs...>();
+  constexpr int P = pad_every<Rs...>();
+  extern __shared__ float2 smem[];
+  const int ly = threadIdx.y;
+  float2* sl = smem + ly * LP;
+  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
+    const int64_t line = base + ly;
+    const bool act = line < a.nlines;
+    const float2* src = reinterpret_cast<const float2*>(a.rin) + line * L;
+    float2* dst = a.cout + line * (L + 1);
+    const int jt = opaque_tid_x();
+    float2 v[emax<L, E, Rs...>()];
+    static_for<0, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            v[q * R + r] = (act && bf_exists<L, E, R>(jt, q)) ? src[jt + q * T + r * (L / R)] : make_float2(0.f, 0.f);
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        line_sync<T>();
+#pragma unroll
+        for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+          if (bf_exists<L, E, Rp>(jt, q))
+#pragma unroll
+            for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+        line_sync<T>();
+#pragma unroll
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
+          if (bf_exists<L, E, R>(jt, q))
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+    line_sync<T>();
+#pragma unroll
+    for (int q = 0; q < nbf<L, E, RL>(); ++q)
+      if (bf_exists<L, E, RL>(jt, q))
+#pragma unroll
+        for (int r = 0; r < RL; ++r) sl[padp<P>(jt + q * T + r * (L / RL))] = v[q * RL + r];
+    line_sync<T>();
+    for (int k = jt; k <= L; k += T) {
+      const float2 zk = sl[padp<P>(k == L ? 0 : k)];
+      const float2 zm = sl[padp<P>(k == 0 ? 0 : L - k)];
+      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));   // (Z[k] + conj Z[L-k]) / 2
+      const float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));   // (Z[k] - conj Z[L-k]) / 2
+      const float2 o = cmul(__ldg(&a.tw2[k]), mul_mi(d));                          // -i w^k d
+      if (act) dst[k] = cscale(cadd(e, o), a.scale);
+    }
+  }
+}
+
+template <int L, int E, int B, int... Rs>
+__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
+    k_c2r_spec(const RealArgs a) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  constexpr int LP = line_pitch<L, Rs...>() + 1;
+  constexpr int P = pad_every<Rs...>();
+  extern __shared__ float2 smem[];
+  const int ly = threadIdx.y;
+  float2* sl = smem + ly * LP;
+  for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
+    const int64_t line = base + ly;
+    const bool act = line < a.nlines;
+    const float2* src = a.cin + line * (L + 1);
+    float2* dst = reinterpret_cast<float2*>(a.rout) + line * L;
+    const int jt = opaque_tid_x();
+    // the L + 1 inputs: every load issued before the first shared store, so
+    // that they are all in flight together
+    constexpr int NK = E + 1;  // ceil((L + 1) / T)
+    float2 xin[NK];
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+      const int k = jt + i * T;
+      xin[i] = (act && k <= L) ? src[k] : make_float2(0.f, 0.f);
+    }
+    line_sync<T>();  // the previous line group is done with sl
+#pragma unroll
+    for (int i = 0; i < NK; ++i) {
+      const int k = jt + i * T;
+      if (k <= L) {
+        float2 x = xin[i];
+        if (k == 0 || k == L) x.y = 0.f;
+        sl[padp<P>(k)] = x;
+      }
+    }
+    line_sync<T>();
+    float2 v[emax<L, E, Rs...>()];
+    static_for<0, NST>([&](auto S) {
+      constexpr int s = decltype(S)::value;
+      constexpr int R = radix_at<s, Rs...>();
+      constexpr int Ns = span_at<s, Rs...>();
+      if constexpr (s == 0) {
+#pragma unroll
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int k = bf_exists<L, E, R>(jt, q) ? jt + q * T + r * (L / R) : 0;
+            const float2 xk = sl[padp<P>(k)];
+            const float2 xm = sl[padp<P>(L - k)];
+            const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);      // X[k] + conj X[L-k]
+            const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);      // X[k] - conj X[L-k]
+            const float2 w = __ldg(&a.tw2[k]);
+            const float2 od = cmul(make_float2(w.x, -w.y), d);           // w^-k d
+            const float2 z = make_float2(e.x - od.y, e.y + od.x);         // e + i w^-k d
+            v[q * R + r] = make_float2(z.x, -z.y);                        // backward = conj o forward o conj
+          }
+      } else {
+        constexpr int Rp = radix_at<s - 1, Rs...>();
+        constexpr int Nsp = Ns / Rp;
+        line_sync<T>();
+#pragma unroll
+        for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+          if (bf_exists<L, E, Rp>(jt, q))
+#pragma unroll
+            for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+        line_sync<T>();
+#pragma unroll
+        for (int q = 0; q < nbf<L, E, R>(); ++q)
+          if (bf_exists<L, E, R>(jt, q))
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
+      }
+      spec_stage<L, E, R, Ns>(v, jt, a.tw);
+    });
+    constexpr int RL = radix_at<NST - 1, Rs...>();
+#pragma unroll
+    for (int q = 0; q < nbf<L, E, RL>(); ++q)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const float2 z = v[q * RL + r];
+        if (act && bf_exists<L, E, RL>(jt, q)) dst[jt + q * T + r * (L / RL)] = make_float2(z.x * a.scale, -z.y * a.scale);
+      }
+  }
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+constexpr int64_t kMaxGrid = 1 << 20;
+
+template <int L, int E, int B, int... Rs>
+cudaError_t run_real(const RealArgs& a, cudaStream_t s) {
+  const int64_t grid0 = (a.nlines + B - 1) / B;
+  const int64_t grid = grid0 > kMaxGrid ? kMaxGrid : grid0;
+  if (grid < 1) return cudaSuccess;
+  if (a.dir < 0) {
+    static cudaError_t attr = allow_smem(k_r2c_spec<L, E, B, Rs...>);
+    if (attr != cudaSuccess) return attr;
+    const size_t smem = (size_t)B * line_pitch<L, Rs...>() * sizeof(float2);
+    k_r2c_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
+  } else {
+    static cudaError_t attr = allow_smem(k_c2r_spec<L, E, B, Rs...>);
+    if (attr != cudaSuccess) return attr;
+    const size_t smem = (size_t)B * (line_pitch<L, Rs...>() + 1) * sizeof(float2);
+    k_c2r_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_real_spec(const RealArgs& a, cudaStream_t s) {
+  switch (a.ap.L) {
+#define X(L, EC, B, ES, W, ...) \
+  case L:                       \
+    return run_real<L, EC, B, __VA_ARGS__>(a, s);
+    TFFT_SPECS(X)
+#undef X
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace tfft

@@ -153,7 +153,7 @@ __device__ __forceinline__ int opaque_tid_y() {
 // (half that for the 20-element plans, whose butterflies need more registers).
 __host__ __device__ constexpr int min_blocks(int E, int threads, int target) {
   const int t = (E >= 20 ? target / 2 : target) / threads;
-  return t > 1 ? t : (E >= 30 && threads <= 256 ? 2 : 1);
+  return t > 1 ? t : (E >= 20 && threads <= 256 ? 2 : 1);
 }
 
 // Synchronises the threads of one line: a warp (or part of one) when a line

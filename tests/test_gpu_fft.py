@@ -35,6 +35,12 @@ CASES = [
     ((96, 160, 64), (2, 2)),         # TMA-staged passes of lengths 96 and 160
     ((60, 120, 240), (2, 4)),        # 2.3.5 lengths: threads with uneven butterfly counts
     ((480, 60, 120), (3, 2)),
+    ((192, 320, 48), (2, 2)),        # specialised lengths 48, 192, 320
+    ((640, 48, 80), (4, 2)),
+    ((768, 4, 384), (2, 2)),
+    ((1024, 8, 64), (2, 2)),
+    ((8, 2048, 8), (2, 2)),
+    ((4096, 4, 8), (4, 2)),          # the longest specialised line, strided
     ((42, 127, 256), (3, 4)),        # the paper's App. A shape: 42 = 2.3.7 and 127 (prime) by Bluestein
     ((7, 11, 26), (2, 3)),           # Bluestein on every axis (26 = 2.13), uneven blocks
     ((2047,), ()),                   # the longest Bluestein line (convolution length 4096)
@@ -219,6 +225,8 @@ def test_full_size_128_4d_sampled(cuda_device):
 
 R2C_CASES = [
     ((8, 12, 480), (2, 2)),          # half-length 240 (2.3.5)
+    ((4, 8, 2048), (2, 2)),          # half-length 1024
+    ((8, 8, 768), (4,)),             # half-length 384
     ((32, 64, 256), (8,)),           # the r2c slab workload's innermost length, 8 ranks
     ((16, 32, 64), (2, 2)),          # r2c on a pencil grid
     ((12, 10, 128), (3,)),           # uneven slab
