@@ -529,6 +529,15 @@ Step box_step(tfft_plan p, const std::vector<BoxDesc>& boxes, size_t off) {
   return s;
 }
 
+// Rows of the inner dimension when an uncut axis of length L > 256 is viewed
+// as two tensor dimensions (L = a x b, both at most 256, a as large as
+// possible); 0 when there is no such split.
+int split_rows(int L) {
+  for (int a = 256; a >= 2; --a)
+    if (L % a == 0 && L / a <= 256) return a;
+  return 0;
+}
+
 // The 5-D view of a stage layout used by the TMA passes exists when d == 3,
 // every cut axis splits evenly, and each rank's innermost extent is a
 // multiple of the tile width (every tile starts on a 16-byte boundary).
@@ -550,10 +559,10 @@ bool tma_geo(tfft_plan p, int stage, int axis, int W, TmaGeo& G) {
     if (G.n[axis] > 256 || p->grid[S.owner[axis]] > 256) return false;
     G.nops = 1;
     G.rows_per_op = L;
-  } else if (L > 256 && L % 256 == 0 && L / 256 <= 256 && axis != 2) {
+  } else if (L > 256 && axis != 2 && split_rows(L) > 0) {
     // one copy per tile: measured, 2 / 4 / 8 copies of 256 / 128 / 64 rows
     // made the 512-row pass take 0.39 / 0.50 / 0.74 ms
-    G.split = 1;
+    G.split = split_rows(L);
     G.nops = 1;
     G.rows_per_op = L;
   } else {
@@ -589,20 +598,20 @@ bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void*
   cuuint64_t strides[4] = {(cuuint64_t)G.n[2] * 8, (cuuint64_t)G.n[1] * G.n[2] * 8, (cuuint64_t)local * 8,
                            (cuuint64_t)local * 8 * D3};
   cuuint32_t box[5] = {(cuuint32_t)W, 1, 1, 1, 1};
-  if (G.split) {  // [rank][outer][axis / 256][256][n2], see TmaGeo
+  if (G.split) {  // [rank][outer][axis / a][a][n2] with a = G.split, see TmaGeo
     const int tax = 1 - axis;  // the other non-innermost axis (d == 3)
     const int64_t sa = axis == 0 ? (int64_t)G.n[1] * G.n[2] : G.n[2];
     const int64_t so = tax == 0 ? (int64_t)G.n[1] * G.n[2] : G.n[2];
-    dims[1] = 256;
-    dims[2] = (cuuint64_t)(G.n[axis] / 256);
+    dims[1] = (cuuint64_t)G.split;
+    dims[2] = (cuuint64_t)(G.n[axis] / G.split);
     dims[3] = (cuuint64_t)G.n[tax];
     dims[4] = (cuuint64_t)p->nranks;
     strides[0] = (cuuint64_t)sa * 8;
-    strides[1] = (cuuint64_t)sa * 256 * 8;
+    strides[1] = (cuuint64_t)sa * G.split * 8;
     strides[2] = (cuuint64_t)so * 8;
     strides[3] = (cuuint64_t)local * 8;
-    box[1] = 256;
-    box[2] = (cuuint32_t)(G.n[axis] / 256);
+    box[1] = (cuuint32_t)G.split;
+    box[2] = (cuuint32_t)(G.n[axis] / G.split);
   } else if (G.cut[axis]) {
     box[2 - axis] = (cuuint32_t)G.n[axis];                             // local rows
     box[G.rdim[axis]] = (cuuint32_t)(p->cshape[axis] / G.n[axis]);     // every rank of the subgroup
@@ -672,10 +681,12 @@ Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
       auto cbt = get_colblocks(p, lin, lout, Wt);
       s.tma_cb_off = cbt.first;
       s.tma_ncb = cbt.second;
-      // measured on 512^3, 4 x 8 grid: the axis-0 pass is faster
-      // with the outer index running fastest, the axis-1 pass with the
-      // column blocks running fastest
-      s.tma_outer_fastest = axis == 0;
+      // measured on 512^3, 4 x 8 grid: the axis-0 pass is faster with the
+      // outer index running fastest (16-column tiles: 0.348 vs 0.356 ms), the
+      // axis-1 pass with the column blocks running fastest; with 8-column
+      // tiles (64-byte rows, 1024 x 1024 x 128) the column-block order wins
+      // on axis 0 as well (0.395 vs 0.588 ms)
+      s.tma_outer_fastest = axis == 0 && Wt * sizeof(float2) >= 128;
     }
   }
   return s;

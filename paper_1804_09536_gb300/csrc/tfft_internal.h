@@ -167,8 +167,9 @@ struct TmaGeo {
   int nops;
   int rows_per_op;
   // split view (uncut FFT axis longer than a 256-row box): the 5-D array is
-  // [rank][outer axis][axis / 256][256][n2] with the rank as one linear index,
-  // so that a whole tile is one copy; rmul[m] = rank stride of cut axis m
+  // [rank][outer axis][axis / split][split][n2] with the rank as one linear
+  // index, so that a whole tile is one copy; rmul[m] = rank stride of cut
+  // axis m; split = 0 for the plain view
   int split;
   int rmul[3];
 };

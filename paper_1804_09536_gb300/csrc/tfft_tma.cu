@@ -201,6 +201,8 @@ cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo
   X(96, 12, 32, 4, 4, 3, 2)     \
   X(128, 16, 32, 16, 8)         \
   X(160, 20, 16, 5, 4, 4, 2)    \
+  X(384, 24, 16, 8, 8, 3, 2)    \
+  X(1024, 32, 8, 32, 32)        \
   X(256, 16, 32, 16, 16)        \
   X(512, 32, 16, 32, 16)        \
   X(512, 16, 16, 8, 8, 8)

@@ -100,7 +100,7 @@ __device__ __forceinline__ void tile_coords(const TmaGeo& G, int axis, int k, in
                                             int tax, int (&c)[5]) {
 #pragma unroll
   for (int i = 0; i < 5; ++i) c[i] = 0;
-  if (G.split) {  // [rank][outer][axis / 256][256][n2]: the whole tile is op 0
+  if (G.split) {  // [rank][outer][axis / split][split][n2]: the whole tile is op 0
     const int64_t pc = G.cut[2] ? col / G.n[2] : 0;
     const int64_t po = G.cut[tax] ? gt / G.n[tax] : 0;
     c[0] = (int)(col - pc * G.n[2]);

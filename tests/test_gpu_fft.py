@@ -41,6 +41,8 @@ CASES = [
     ((1024, 8, 64), (2, 2)),
     ((8, 2048, 8), (2, 2)),
     ((4096, 4, 8), (4, 2)),          # the longest specialised line, strided
+    ((384, 32, 64), (2, 4)),         # TMA-staged 384 (uncut rows viewed as 192 x 2)
+    ((1024, 16, 32), (2, 2)),        # TMA-staged 1024 (256 x 4), 8-column tiles
     ((42, 127, 256), (3, 4)),        # the paper's App. A shape: 42 = 2.3.7 and 127 (prime) by Bluestein
     ((7, 11, 26), (2, 3)),           # Bluestein on every axis (26 = 2.13), uneven blocks
     ((2047,), ()),                   # the longest Bluestein line (convolution length 4096)
@@ -84,7 +86,8 @@ def test_forward_inverse_vs_oracle(cuda_device, shape, grid):
 
 
 @pytest.mark.parametrize("shape,grid", [((256, 128, 256), (2, 4)), ((512, 64, 64), (4, 2)),
-                                        ((64, 64, 64), (2, 2)), ((128, 512, 64), (2, 2))])
+                                        ((64, 64, 64), (2, 2)), ((128, 512, 64), (2, 2)),
+                                        ((384, 32, 64), (2, 4)), ((1024, 16, 32), (2, 2))])
 def test_tma_and_plain_passes_identical(cuda_device, shape, grid):
     """The TMA-staged passes and the plain load/store passes run the same
     butterflies on every line: forward and inverse outputs are bit-identical."""
