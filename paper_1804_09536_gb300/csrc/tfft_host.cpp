@@ -7,6 +7,8 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <new>
+#include <stdexcept>
 #include <numeric>
 #include <string>
 #include <tuple>
@@ -985,6 +987,21 @@ BlueArgs blue_args(tfft_plan p, int N) {
 
 // ============================================================== ABI
 
+// Runs an entry point's body so that no C++ exception (host allocation
+// failure, a library error) crosses the C ABI: it becomes an error status.
+template <class F>
+int guarded(const char* name, F&& body) {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return fail(TFFT_EINVAL, std::string(name) + ": out of host memory");
+  } catch (const std::exception& e) {
+    return fail(TFFT_EINVAL, std::string(name) + ": " + e.what());
+  } catch (...) {
+    return fail(TFFT_EINVAL, std::string(name) + ": unexpected error");
+  }
+}
+
 extern "C" {
 
 const char* tfft_status_string(int status) {
@@ -1013,137 +1030,139 @@ int tfft_decompose(int64_t N, int64_t M, int64_t p, int64_t* n, int64_t* s) {
 
 int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_ndims,
                      const int* grid, int kind, int precision, int flags) {
-  if (!plan) return fail(TFFT_EINVAL, "plan is NULL");
-  *plan = nullptr;
-  if (ndims < 1 || ndims > MAXD) return fail(TFFT_EINVAL, "ndims must be 1..4");
-  if (!shape) return fail(TFFT_EINVAL, "shape is NULL");
-  if (grid_ndims < 0 || grid_ndims > ndims - 1 || grid_ndims > MAXG)
-    return fail(TFFT_EINVAL, "grid_ndims must be 0..min(3, ndims - 1) (Sec. 3.6)");
-  if (grid_ndims > 0 && !grid) return fail(TFFT_EINVAL, "grid is NULL");
-  if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
-  if (precision != TFFT_FP32 && precision != TFFT_TC_BF16X3 && precision != TFFT_TC_FP16X3)
-    return fail(TFFT_EINVAL, "precision must be TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3");
-  if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA)) return fail(TFFT_EINVAL, "unknown flag bits");
-  auto p = new tfft_plan_s();
-  p->d = ndims;
-  p->g = grid_ndims;
-  p->kind = kind;
-  p->precision = precision;
-  p->flags = flags;
-  int64_t n = 1;
-  for (int m = 0; m < ndims; ++m) {
-    if (shape[m] < 1 || shape[m] > (int64_t(1) << 31)) {
-      delete p;
-      return fail(TFFT_EINVAL, "every extent must be in 1 .. 2^31");
-    }
-    p->shape[m] = p->cshape[m] = shape[m];
-    n *= shape[m];
-  }
-  p->nreal = n;
-  if (kind == TFFT_R2C) {
-    if (shape[ndims - 1] % 2) {
-      delete p;
-      return fail(TFFT_EUNSUPPORTED, "real-to-complex needs an even innermost extent");
-    }
-    p->cshape[ndims - 1] = shape[ndims - 1] / 2 + 1;  // Hermitian half (footnote to Eq. multifft)
-    n = n / shape[ndims - 1] * p->cshape[ndims - 1];
-  }
-  p->nelems = n;
-  int64_t nr = 1;
-  for (int i = 0; i < grid_ndims; ++i) {
-    if (grid[i] < 1 || grid[i] > 65536) {
-      delete p;
-      return fail(TFFT_EINVAL, "grid extents must be in 1 .. 65536");
-    }
-    p->grid[i] = grid[i];
-    nr *= grid[i];
-  }
-  if (nr > (1 << 20)) {
-    delete p;
-    return fail(TFFT_EINVAL, "too many virtual ranks");
-  }
-  p->nranks = (int)nr;
-  for (int i = grid_ndims - 1, s = 1; i >= 0; --i) {
-    p->rstride[i] = s;
-    s *= grid[i];
-  }
-  // stage layouts and their rank offset tables
-  p->use_tma = !(flags & TFFT_NO_TMA);
-  image_add(p, nullptr, 256);  // device status word(s) at offset 0
-  p->red_off = image_add(p, nullptr, kReductionParts * sizeof(double));
-  p->st.resize(p->g + 1);
-  for (int s = 0; s <= p->g; ++s) {
-    build_layout(p, p->cshape, s, p->st[s]);
-    p->st[s].state_off = image_add(p, p->st[s].offset.data(), p->st[s].offset.size() * 8);
-  }
-  if (kind == TFFT_R2C) build_layout(p, p->shape, 0, p->real0);
-  // per-length FFT plans and twiddle table slots (a plan whose lengths do not
-  // factor into 2, 3, 5 up to 4096 still redistributes, but does not transform)
-  if (kind == TFFT_R2C) {
-    const int Lh = (int)(p->shape[ndims - 1] / 2);
-    int width = 0;
-    p->rplan = AxisPlan{};
-    if (spec_plan(Lh, false, p->nelems, p->rplan, width)) {
-      p->rplan.width = width;
-      if (!p->tw_off.count(Lh)) p->tw_off[Lh] = image_add(p, nullptr, (size_t)Lh * sizeof(float2));
-      if (!p->tw_off.count(2 * Lh)) p->tw_off[2 * Lh] = image_add(p, nullptr, (size_t)2 * Lh * sizeof(float2));
-    } else {
-      p->transformable = false;  // half length without a compiled real-line kernel
-    }
-  }
-  for (int m = 0; m < ndims; ++m) {
-    if (kind == TFFT_R2C && m == ndims - 1) break;  // the innermost axis is the real pass
-    const int L = (int)p->cshape[m];
-    if (p->aplan.count(L)) continue;
-    AxisPlan ap{}, aps{};
-    if (!is_smooth_235(L) && L <= MAXLEN / 2) {
-      if (!make_bluestein(p, L)) p->transformable = false;
-      continue;
-    }
-    if (L > MAXLEN || !is_smooth_235(L) || !make_axis_plan(L, false, ap) ||
-        !make_axis_plan(L, true, aps)) {
-      p->transformable = false;
-      continue;
-    }
-    int width = 0;
-    if (spec_plan(L, false, p->nelems, ap, width)) ap.width = width;
-    if (spec_plan(L, true, p->nelems, aps, width)) aps.width = width;
-    p->aplan[L] = ap;
-    p->aplan_s[L] = aps;
-    if (!p->tw_off.count(L)) p->tw_off[L] = image_add(p, nullptr, (size_t)L * sizeof(float2));
-  }
-  // exchange boxes between adjacent stages, both directions
-  for (int s = 1; s <= p->g; ++s) {
-    build_exchange(p, s - 1, s);
-    build_exchange(p, s, s - 1);
-  }
-  if (p->transformable) {
-    // pass lists
-    for (int sign : {TFFT_FORWARD, TFFT_BACKWARD})
-      for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED})
-        p->steps[{sign, mode}] = build_steps(p, sign, mode);
-    // the adjoint of the forward (kAdjoint): the backward steps, with 1/N on
-    // the last pass when the forward carries the normalisation
-    if (p->kind == TFFT_C2C)
-      for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED}) {
-        std::vector<Step> v = build_steps(p, TFFT_BACKWARD, mode);
-        if (!(p->flags & TFFT_NORM_BACKWARD))
-          for (int k = (int)v.size() - 1; k >= 0; --k)
-            if (v[k].kind != S_BOX) {
-              v[k].scaled = true;
-              v[k].scale_value = 1.0 / (double)p->nelems;
-              break;
-            }
-        p->steps[{kAdjoint, mode}] = v;
+  return guarded("tfft_plan_create", [&]() -> int {
+    if (!plan) return fail(TFFT_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    if (ndims < 1 || ndims > MAXD) return fail(TFFT_EINVAL, "ndims must be 1..4");
+    if (!shape) return fail(TFFT_EINVAL, "shape is NULL");
+    if (grid_ndims < 0 || grid_ndims > ndims - 1 || grid_ndims > MAXG)
+      return fail(TFFT_EINVAL, "grid_ndims must be 0..min(3, ndims - 1) (Sec. 3.6)");
+    if (grid_ndims > 0 && !grid) return fail(TFFT_EINVAL, "grid is NULL");
+    if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
+    if (precision != TFFT_FP32 && precision != TFFT_TC_BF16X3 && precision != TFFT_TC_FP16X3)
+      return fail(TFFT_EINVAL, "precision must be TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3");
+    if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA)) return fail(TFFT_EINVAL, "unknown flag bits");
+    auto p = new tfft_plan_s();
+    p->d = ndims;
+    p->g = grid_ndims;
+    p->kind = kind;
+    p->precision = precision;
+    p->flags = flags;
+    int64_t n = 1;
+    for (int m = 0; m < ndims; ++m) {
+      if (shape[m] < 1 || shape[m] > (int64_t(1) << 31)) {
+        delete p;
+        return fail(TFFT_EINVAL, "every extent must be in 1 .. 2^31");
       }
-    // column blocks for in-place partial transforms of every stage
-    for (int s = 0; s <= p->g; ++s)
-      for (auto& kv : p->aplan_s) get_colblocks(p, s, s, strided_width(kv.second));
-  }
-  p->state_bytes = align_up(p->image.size(), 256);
-  p->image.resize(p->state_bytes, 0);
-  *plan = p;
-  return TFFT_OK;
+      p->shape[m] = p->cshape[m] = shape[m];
+      n *= shape[m];
+    }
+    p->nreal = n;
+    if (kind == TFFT_R2C) {
+      if (shape[ndims - 1] % 2) {
+        delete p;
+        return fail(TFFT_EUNSUPPORTED, "real-to-complex needs an even innermost extent");
+      }
+      p->cshape[ndims - 1] = shape[ndims - 1] / 2 + 1;  // Hermitian half (footnote to Eq. multifft)
+      n = n / shape[ndims - 1] * p->cshape[ndims - 1];
+    }
+    p->nelems = n;
+    int64_t nr = 1;
+    for (int i = 0; i < grid_ndims; ++i) {
+      if (grid[i] < 1 || grid[i] > 65536) {
+        delete p;
+        return fail(TFFT_EINVAL, "grid extents must be in 1 .. 65536");
+      }
+      p->grid[i] = grid[i];
+      nr *= grid[i];
+    }
+    if (nr > (1 << 20)) {
+      delete p;
+      return fail(TFFT_EINVAL, "too many virtual ranks");
+    }
+    p->nranks = (int)nr;
+    for (int i = grid_ndims - 1, s = 1; i >= 0; --i) {
+      p->rstride[i] = s;
+      s *= grid[i];
+    }
+    // stage layouts and their rank offset tables
+    p->use_tma = !(flags & TFFT_NO_TMA);
+    image_add(p, nullptr, 256);  // device status word(s) at offset 0
+    p->red_off = image_add(p, nullptr, kReductionParts * sizeof(double));
+    p->st.resize(p->g + 1);
+    for (int s = 0; s <= p->g; ++s) {
+      build_layout(p, p->cshape, s, p->st[s]);
+      p->st[s].state_off = image_add(p, p->st[s].offset.data(), p->st[s].offset.size() * 8);
+    }
+    if (kind == TFFT_R2C) build_layout(p, p->shape, 0, p->real0);
+    // per-length FFT plans and twiddle table slots (a plan whose lengths do not
+    // factor into 2, 3, 5 up to 4096 still redistributes, but does not transform)
+    if (kind == TFFT_R2C) {
+      const int Lh = (int)(p->shape[ndims - 1] / 2);
+      int width = 0;
+      p->rplan = AxisPlan{};
+      if (spec_plan(Lh, false, p->nelems, p->rplan, width)) {
+        p->rplan.width = width;
+        if (!p->tw_off.count(Lh)) p->tw_off[Lh] = image_add(p, nullptr, (size_t)Lh * sizeof(float2));
+        if (!p->tw_off.count(2 * Lh)) p->tw_off[2 * Lh] = image_add(p, nullptr, (size_t)2 * Lh * sizeof(float2));
+      } else {
+        p->transformable = false;  // half length without a compiled real-line kernel
+      }
+    }
+    for (int m = 0; m < ndims; ++m) {
+      if (kind == TFFT_R2C && m == ndims - 1) break;  // the innermost axis is the real pass
+      const int L = (int)p->cshape[m];
+      if (p->aplan.count(L)) continue;
+      AxisPlan ap{}, aps{};
+      if (!is_smooth_235(L) && L <= MAXLEN / 2) {
+        if (!make_bluestein(p, L)) p->transformable = false;
+        continue;
+      }
+      if (L > MAXLEN || !is_smooth_235(L) || !make_axis_plan(L, false, ap) ||
+          !make_axis_plan(L, true, aps)) {
+        p->transformable = false;
+        continue;
+      }
+      int width = 0;
+      if (spec_plan(L, false, p->nelems, ap, width)) ap.width = width;
+      if (spec_plan(L, true, p->nelems, aps, width)) aps.width = width;
+      p->aplan[L] = ap;
+      p->aplan_s[L] = aps;
+      if (!p->tw_off.count(L)) p->tw_off[L] = image_add(p, nullptr, (size_t)L * sizeof(float2));
+    }
+    // exchange boxes between adjacent stages, both directions
+    for (int s = 1; s <= p->g; ++s) {
+      build_exchange(p, s - 1, s);
+      build_exchange(p, s, s - 1);
+    }
+    if (p->transformable) {
+      // pass lists
+      for (int sign : {TFFT_FORWARD, TFFT_BACKWARD})
+        for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED})
+          p->steps[{sign, mode}] = build_steps(p, sign, mode);
+      // the adjoint of the forward (kAdjoint): the backward steps, with 1/N on
+      // the last pass when the forward carries the normalisation
+      if (p->kind == TFFT_C2C)
+        for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED}) {
+          std::vector<Step> v = build_steps(p, TFFT_BACKWARD, mode);
+          if (!(p->flags & TFFT_NORM_BACKWARD))
+            for (int k = (int)v.size() - 1; k >= 0; --k)
+              if (v[k].kind != S_BOX) {
+                v[k].scaled = true;
+                v[k].scale_value = 1.0 / (double)p->nelems;
+                break;
+              }
+          p->steps[{kAdjoint, mode}] = v;
+        }
+      // column blocks for in-place partial transforms of every stage
+      for (int s = 0; s <= p->g; ++s)
+        for (auto& kv : p->aplan_s) get_colblocks(p, s, s, strided_width(kv.second));
+    }
+    p->state_bytes = align_up(p->image.size(), 256);
+    p->image.resize(p->state_bytes, 0);
+    *plan = p;
+    return TFFT_OK;
+  });
 }
 
 int tfft_plan_destroy(tfft_plan plan) {
@@ -1207,21 +1226,23 @@ int tfft_plan_state_bytes(tfft_plan p, size_t* bytes) {
 }
 
 int tfft_plan_bind(tfft_plan p, void* d_state, size_t bytes, void* stream) {
-  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  int rc = check_ptr(d_state, "d_state");
-  if (rc) return rc;
-  if (bytes < p->state_bytes) return fail(TFFT_EINVAL, "state buffer too small");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(d_state, p->image.data(), p->state_bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (plan state)");
-  for (auto& kv : p->tw_off) {
-    e = launch_twiddles(reinterpret_cast<float2*>(static_cast<char*>(d_state) + kv.second), kv.first, st);
-    if (e != cudaSuccess) return cuda_fail(e, "twiddle generation");
-  }
-  e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (bind)");
-  p->d_state = static_cast<char*>(d_state);
-  return TFFT_OK;
+  return guarded("tfft_plan_bind", [&]() -> int {
+    if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+    int rc = check_ptr(d_state, "d_state");
+    if (rc) return rc;
+    if (bytes < p->state_bytes) return fail(TFFT_EINVAL, "state buffer too small");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d_state, p->image.data(), p->state_bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (plan state)");
+    for (auto& kv : p->tw_off) {
+      e = launch_twiddles(reinterpret_cast<float2*>(static_cast<char*>(d_state) + kv.second), kv.first, st);
+      if (e != cudaSuccess) return cuda_fail(e, "twiddle generation");
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (bind)");
+    p->d_state = static_cast<char*>(d_state);
+    return TFFT_OK;
+  });
 }
 
 int tfft_plan_workspace_bytes(tfft_plan p, int mode, int keep_input, size_t* bytes) {
@@ -1237,47 +1258,51 @@ int tfft_plan_workspace_bytes(tfft_plan p, int mode, int keep_input, size_t* byt
 }
 
 int tfft_redistribute(tfft_plan p, int axis_v, int axis_w, const void* in, void* out, void* stream) {
-  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
-  const int sf = p->g - axis_v, stt = p->g - axis_w;
-  if (sf < 0 || sf > p->g || stt < 0 || stt > p->g || std::abs(sf - stt) != 1)
-    return fail(TFFT_EINVAL, "axis_v / axis_w are not the aligned axes of two adjacent stages");
-  int rc = check_ptr(in, "in");
-  if (rc) return rc;
-  rc = check_ptr(out, "out");
-  if (rc) return rc;
-  const size_t bytes = (size_t)p->nelems * sizeof(float2);
-  const char* a = static_cast<const char*>(in);
-  const char* b = static_cast<const char*>(out);
-  if (a < b + bytes && b < a + bytes) return fail(TFFT_EINVAL, "in and out overlap");
-  const ExchangeBoxes& X = p->xboxes[{sf, stt}];
-  Step s = box_step(p, X.direct, p->xbox_off[{sf, stt}][0]);
-  s.src = BUF_IN;
-  s.dst = BUF_OUT;
-  void* bufs[4] = {const_cast<void*>(in), out, nullptr, nullptr};
-  return launch_step(p, s, bufs, static_cast<cudaStream_t>(stream));
+  return guarded("tfft_redistribute", [&]() -> int {
+    if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    const int sf = p->g - axis_v, stt = p->g - axis_w;
+    if (sf < 0 || sf > p->g || stt < 0 || stt > p->g || std::abs(sf - stt) != 1)
+      return fail(TFFT_EINVAL, "axis_v / axis_w are not the aligned axes of two adjacent stages");
+    int rc = check_ptr(in, "in");
+    if (rc) return rc;
+    rc = check_ptr(out, "out");
+    if (rc) return rc;
+    const size_t bytes = (size_t)p->nelems * sizeof(float2);
+    const char* a = static_cast<const char*>(in);
+    const char* b = static_cast<const char*>(out);
+    if (a < b + bytes && b < a + bytes) return fail(TFFT_EINVAL, "in and out overlap");
+    const ExchangeBoxes& X = p->xboxes[{sf, stt}];
+    Step s = box_step(p, X.direct, p->xbox_off[{sf, stt}][0]);
+    s.src = BUF_IN;
+    s.dst = BUF_OUT;
+    void* bufs[4] = {const_cast<void*>(in), out, nullptr, nullptr};
+    return launch_step(p, s, bufs, static_cast<cudaStream_t>(stream));
+  });
 }
 
 int tfft_partial(tfft_plan p, int stage, int axis, int sign, void* inout, void* stream) {
-  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
-  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
-  if (axis < 0 || axis >= p->d) return fail(TFFT_EINVAL, "axis out of range");
-  if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
-  if (p->st[stage].owner[axis] >= 0) return fail(TFFT_EINVAL, "axis is distributed in this stage");
-  if (!p->aplan.count((int)p->cshape[axis]))
-    return fail(TFFT_EUNSUPPORTED, "axis length is not a product of 2, 3, 5 up to 4096");
-  int rc = check_ptr(inout, "inout");
-  if (rc) return rc;
-  Step s = fft_step(p, axis, stage, stage, sign);
-  s.src = BUF_IN;
-  s.dst = BUF_IN;
-  if (sign == TFFT_FORWARD) {
-    s.scaled = true;
-    s.scale_value = 1.0 / (double)p->cshape[axis];
-  }
-  void* bufs[4] = {inout, inout, nullptr, nullptr};
-  return launch_step(p, s, bufs, static_cast<cudaStream_t>(stream));
+  return guarded("tfft_partial", [&]() -> int {
+    if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+    if (axis < 0 || axis >= p->d) return fail(TFFT_EINVAL, "axis out of range");
+    if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
+    if (p->st[stage].owner[axis] >= 0) return fail(TFFT_EINVAL, "axis is distributed in this stage");
+    if (!p->aplan.count((int)p->cshape[axis]))
+      return fail(TFFT_EUNSUPPORTED, "axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
+    int rc = check_ptr(inout, "inout");
+    if (rc) return rc;
+    Step s = fft_step(p, axis, stage, stage, sign);
+    s.src = BUF_IN;
+    s.dst = BUF_IN;
+    if (sign == TFFT_FORWARD) {
+      s.scaled = true;
+      s.scale_value = 1.0 / (double)p->cshape[axis];
+    }
+    void* bufs[4] = {inout, inout, nullptr, nullptr};
+    return launch_step(p, s, bufs, static_cast<cudaStream_t>(stream));
+  });
 }
 
 int tfft_plan_num_launches(tfft_plan p, int sign, int mode, int* n) {
@@ -1291,51 +1316,53 @@ int tfft_plan_num_launches(tfft_plan p, int sign, int mode, int* n) {
 
 int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name, int name_len,
                           int64_t* bytes) {
-  if (!p || !bytes || (name_len > 0 && !name)) return fail(TFFT_EINVAL, "NULL argument");
-  if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
-  auto it = p->steps.find({sign, mode});
-  if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
-  if (index < 0 || index >= (int)it->second.size()) return fail(TFFT_EINVAL, "launch index out of range");
-  const Step& s = it->second[index];
-  std::string nm;
-  int64_t elems = 0;
-  if (s.kind == S_REAL) {
-    nm = std::string(sign == TFFT_FORWARD ? "fft_r2c_L" : "fft_c2r_L") + std::to_string(2 * p->rplan.L);
-    *bytes = p->nreal * (int64_t)sizeof(float) + p->nelems * (int64_t)sizeof(float2);
+  return guarded("tfft_plan_launch_info", [&]() -> int {
+    if (!p || !bytes || (name_len > 0 && !name)) return fail(TFFT_EINVAL, "NULL argument");
+    if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
+    auto it = p->steps.find({sign, mode});
+    if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
+    if (index < 0 || index >= (int)it->second.size()) return fail(TFFT_EINVAL, "launch index out of range");
+    const Step& s = it->second[index];
+    std::string nm;
+    int64_t elems = 0;
+    if (s.kind == S_REAL) {
+      nm = std::string(sign == TFFT_FORWARD ? "fft_r2c_L" : "fft_c2r_L") + std::to_string(2 * p->rplan.L);
+      *bytes = p->nreal * (int64_t)sizeof(float) + p->nelems * (int64_t)sizeof(float2);
+      if (name_len > 0) {
+        std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
+        name[name_len - 1] = 0;
+      }
+      return TFFT_OK;
+    }
+    if (s.kind == S_BOX) {
+      nm = "box_copy";
+      const ExchangeBoxes* X = nullptr;
+      for (auto& kv : p->xbox_off)
+        for (int k = 0; k < 4; ++k)
+          if (kv.second[k] == s.box_off) {
+            const ExchangeBoxes& E = p->xboxes[kv.first];
+            const std::vector<BoxDesc>* v[4] = {&E.direct, &E.pack, &E.xchg, &E.unpack};
+            for (const BoxDesc& b : *v[k]) elems += b.ext[0] * b.ext[1] * b.ext[2] * b.ext[3];
+            X = &E;
+          }
+      (void)X;
+    } else {
+      const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
+      const bool tma = s.kind == S_STRIDED && s.tma;
+      const bool tc = s.kind == S_CONTIG && p->precision != TFFT_FP32 && tc_supported(ap.L);
+      nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
+           (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : tma ? "_tma" : "") +
+           (ap.spec ? "_L" + std::to_string(ap.L) : ap.E == 0 ? std::string("_generic")
+                                                              : "_E" + std::to_string(ap.E));
+      elems = p->nelems;
+    }
+    *bytes = 2 * elems * (int64_t)sizeof(float2);  // one read and one write of every element
     if (name_len > 0) {
       std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
       name[name_len - 1] = 0;
     }
     return TFFT_OK;
-  }
-  if (s.kind == S_BOX) {
-    nm = "box_copy";
-    const ExchangeBoxes* X = nullptr;
-    for (auto& kv : p->xbox_off)
-      for (int k = 0; k < 4; ++k)
-        if (kv.second[k] == s.box_off) {
-          const ExchangeBoxes& E = p->xboxes[kv.first];
-          const std::vector<BoxDesc>* v[4] = {&E.direct, &E.pack, &E.xchg, &E.unpack};
-          for (const BoxDesc& b : *v[k]) elems += b.ext[0] * b.ext[1] * b.ext[2] * b.ext[3];
-          X = &E;
-        }
-    (void)X;
-  } else {
-    const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
-    const bool tma = s.kind == S_STRIDED && s.tma;
-    const bool tc = s.kind == S_CONTIG && p->precision != TFFT_FP32 && tc_supported(ap.L);
-    nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
-         (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : tma ? "_tma" : "") +
-         (ap.spec ? "_L" + std::to_string(ap.L) : ap.E == 0 ? std::string("_generic")
-                                                            : "_E" + std::to_string(ap.E));
-    elems = p->nelems;
-  }
-  *bytes = 2 * elems * (int64_t)sizeof(float2);  // one read and one write of every element
-  if (name_len > 0) {
-    std::strncpy(name, nm.c_str(), (size_t)name_len - 1);
-    name[name_len - 1] = 0;
-  }
-  return TFFT_OK;
+  });
 }
 
 int tfft_plan_set_wait_limit(tfft_plan p, uint32_t polls) {
@@ -1377,14 +1404,18 @@ static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in
 
 int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, void* work,
                  size_t work_bytes, void* stream) {
-  return execute_impl(p, sign, sign, mode, in, out, work, work_bytes, stream);
+  return guarded("tfft_execute", [&]() -> int {
+    return execute_impl(p, sign, sign, mode, in, out, work, work_bytes, stream);
+  });
 }
 
 int tfft_adjoint(tfft_plan p, int mode, const void* in, void* out, void* work, size_t work_bytes,
                  const double* d_coef, void* stream) {
-  if (p && p->kind != TFFT_C2C) return fail(TFFT_EUNSUPPORTED, "the adjoint is built for complex-to-complex plans");
-  if (d_coef && (reinterpret_cast<uintptr_t>(d_coef) & 7)) return fail(TFFT_EINVAL, "d_coef is misaligned");
-  return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, in, out, work, work_bytes, stream, d_coef);
+  return guarded("tfft_adjoint", [&]() -> int {
+    if (p && p->kind != TFFT_C2C) return fail(TFFT_EUNSUPPORTED, "the adjoint is built for complex-to-complex plans");
+    if (d_coef && (reinterpret_cast<uintptr_t>(d_coef) & 7)) return fail(TFFT_EINVAL, "d_coef is misaligned");
+    return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, in, out, work, work_bytes, stream, d_coef);
+  });
 }
 
 // ---------------------------------------------------------------- host buffers
@@ -1437,98 +1468,104 @@ int tfft_host_space_bytes(tfft_plan p, size_t* bytes) {
 
 int tfft_execute_host(tfft_plan p, int nsigns, const int* signs, int count, const void* const* h_in,
                       void* const* h_out, void* d_space, size_t space_bytes, void* stream) {
-  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
-  if (nsigns < 1 || !signs) return fail(TFFT_EINVAL, "need at least one transform direction");
-  for (int j = 0; j < nsigns; ++j) {
-    if (signs[j] != TFFT_FORWARD && signs[j] != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
-    if (j > 0 && signs[j] == signs[j - 1])
-      return fail(TFFT_EINVAL, "directions must alternate (a forward leaves stage g, a backward stage 0)");
-  }
-  if (count < 0 || (count > 0 && (!h_in || !h_out))) return fail(TFFT_EINVAL, "bad host buffer lists");
-  int rc = check_ptr(d_space, "d_space");
-  if (rc) return rc;
-  const size_t B = host_buf_bytes(p);
-  if (space_bytes < 2 * kHostSetBufs * B) return fail(TFFT_EWORKSPACE, "d_space smaller than tfft_host_space_bytes");
-  for (int k = 0; k < count; ++k) {
-    if ((rc = check_pinned(h_in[k], "h_in")) || (rc = check_pinned(h_out[k], "h_out"))) return rc;
-  }
-  if (count == 0) return TFFT_OK;
-  if ((rc = ensure_host_io(p))) return rc;
-  auto& io = p->io;
-  const bool r2c = p->kind == TFFT_R2C;
-  const size_t cbytes = (size_t)p->nelems * sizeof(float2), rbytes = (size_t)p->nreal * sizeof(float);
-  const size_t in_bytes = (r2c && signs[0] == TFFT_FORWARD) ? rbytes : cbytes;
-  const size_t out_bytes = (r2c && signs[nsigns - 1] == TFFT_BACKWARD) ? rbytes : cbytes;
-  cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  auto ok = [](cudaError_t e) { return e == cudaSuccess; };
-  cudaError_t e = cudaEventRecord(io.start, cs);  // after the caller's earlier work
-  if (ok(e)) e = cudaStreamWaitEvent(io.cin, io.start, 0);
-  if (ok(e)) e = cudaStreamWaitEvent(io.cout, io.start, 0);
-  // array k uses buffer set k % 2: its copy-in overlaps the transform of array
-  // k - 1 and the copy-out of array k - 2
-  for (int k = 0; k < count && ok(e); ++k) {
-    const int s = k & 1;
-    char* base = static_cast<char*>(d_space) + (size_t)s * kHostSetBufs * B;
-    char* bin = base;
-    char* bmid = base + B;
-    char* bout = base + 2 * B;
-    char* bwork = base + 3 * B;
-    if (k >= 2) e = cudaStreamWaitEvent(io.cin, io.comp_done[s], 0);  // array k-2 is done with bin
-    if (ok(e)) e = cudaMemcpyAsync(bin, h_in[k], in_bytes, cudaMemcpyHostToDevice, io.cin);
-    if (ok(e)) e = cudaEventRecord(io.in_done[s], io.cin);
-    if (ok(e)) e = cudaStreamWaitEvent(cs, io.in_done[s], 0);
-    if (ok(e) && k >= 2) e = cudaStreamWaitEvent(cs, io.out_done[s], 0);  // bout copied out
-    if (!ok(e)) break;
-    char* src = bin;
+  return guarded("tfft_execute_host", [&]() -> int {
+    if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (nsigns < 1 || !signs) return fail(TFFT_EINVAL, "need at least one transform direction");
     for (int j = 0; j < nsigns; ++j) {
-      char* dst = (j == nsigns - 1) ? bout : ((j % 2 == 0) ? bmid : bin);
-      rc = execute_impl(p, signs[j], signs[j], TFFT_MODE_FUSED, src, dst, bwork, B, stream);
-      if (rc) return rc;
-      src = dst;
+      if (signs[j] != TFFT_FORWARD && signs[j] != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
+      if (j > 0 && signs[j] == signs[j - 1])
+        return fail(TFFT_EINVAL, "directions must alternate (a forward leaves stage g, a backward stage 0)");
     }
-    e = cudaEventRecord(io.comp_done[s], cs);
-    if (ok(e)) e = cudaStreamWaitEvent(io.cout, io.comp_done[s], 0);
-    if (ok(e)) e = cudaMemcpyAsync(h_out[k], bout, out_bytes, cudaMemcpyDeviceToHost, io.cout);
-    if (ok(e)) e = cudaEventRecord(io.out_done[s], io.cout);
-  }
-  if (ok(e)) e = cudaEventRecord(io.end, io.cout);
-  if (ok(e)) e = cudaStreamWaitEvent(cs, io.end, 0);  // the caller's stream sees the copied results
-  if (!ok(e)) return cuda_fail(e, "tfft_execute_host");
-  return TFFT_OK;
+    if (count < 0 || (count > 0 && (!h_in || !h_out))) return fail(TFFT_EINVAL, "bad host buffer lists");
+    int rc = check_ptr(d_space, "d_space");
+    if (rc) return rc;
+    const size_t B = host_buf_bytes(p);
+    if (space_bytes < 2 * kHostSetBufs * B) return fail(TFFT_EWORKSPACE, "d_space smaller than tfft_host_space_bytes");
+    for (int k = 0; k < count; ++k) {
+      if ((rc = check_pinned(h_in[k], "h_in")) || (rc = check_pinned(h_out[k], "h_out"))) return rc;
+    }
+    if (count == 0) return TFFT_OK;
+    if ((rc = ensure_host_io(p))) return rc;
+    auto& io = p->io;
+    const bool r2c = p->kind == TFFT_R2C;
+    const size_t cbytes = (size_t)p->nelems * sizeof(float2), rbytes = (size_t)p->nreal * sizeof(float);
+    const size_t in_bytes = (r2c && signs[0] == TFFT_FORWARD) ? rbytes : cbytes;
+    const size_t out_bytes = (r2c && signs[nsigns - 1] == TFFT_BACKWARD) ? rbytes : cbytes;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    cudaError_t e = cudaEventRecord(io.start, cs);  // after the caller's earlier work
+    if (ok(e)) e = cudaStreamWaitEvent(io.cin, io.start, 0);
+    if (ok(e)) e = cudaStreamWaitEvent(io.cout, io.start, 0);
+    // array k uses buffer set k % 2: its copy-in overlaps the transform of array
+    // k - 1 and the copy-out of array k - 2
+    for (int k = 0; k < count && ok(e); ++k) {
+      const int s = k & 1;
+      char* base = static_cast<char*>(d_space) + (size_t)s * kHostSetBufs * B;
+      char* bin = base;
+      char* bmid = base + B;
+      char* bout = base + 2 * B;
+      char* bwork = base + 3 * B;
+      if (k >= 2) e = cudaStreamWaitEvent(io.cin, io.comp_done[s], 0);  // array k-2 is done with bin
+      if (ok(e)) e = cudaMemcpyAsync(bin, h_in[k], in_bytes, cudaMemcpyHostToDevice, io.cin);
+      if (ok(e)) e = cudaEventRecord(io.in_done[s], io.cin);
+      if (ok(e)) e = cudaStreamWaitEvent(cs, io.in_done[s], 0);
+      if (ok(e) && k >= 2) e = cudaStreamWaitEvent(cs, io.out_done[s], 0);  // bout copied out
+      if (!ok(e)) break;
+      char* src = bin;
+      for (int j = 0; j < nsigns; ++j) {
+        char* dst = (j == nsigns - 1) ? bout : ((j % 2 == 0) ? bmid : bin);
+        rc = execute_impl(p, signs[j], signs[j], TFFT_MODE_FUSED, src, dst, bwork, B, stream);
+        if (rc) return rc;
+        src = dst;
+      }
+      e = cudaEventRecord(io.comp_done[s], cs);
+      if (ok(e)) e = cudaStreamWaitEvent(io.cout, io.comp_done[s], 0);
+      if (ok(e)) e = cudaMemcpyAsync(h_out[k], bout, out_bytes, cudaMemcpyDeviceToHost, io.cout);
+      if (ok(e)) e = cudaEventRecord(io.out_done[s], io.cout);
+    }
+    if (ok(e)) e = cudaEventRecord(io.end, io.cout);
+    if (ok(e)) e = cudaStreamWaitEvent(cs, io.end, 0);  // the caller's stream sees the copied results
+    if (!ok(e)) return cuda_fail(e, "tfft_execute_host");
+    return TFFT_OK;
+  });
 }
 
 int tfft_weighted_energy(tfft_plan p, int stage, const void* y, const float* w, double* d_loss, void* u,
                          void* stream) {
-  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
-  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
-  int rc = check_ptr(y, "y");
-  if (rc) return rc;
-  if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
-  if (!d_loss || (reinterpret_cast<uintptr_t>(d_loss) & 7)) return fail(TFFT_EINVAL, "d_loss is NULL or misaligned");
-  if (u && (rc = check_ptr(u, "u"))) return rc;
-  cudaError_t e = launch_weighted_energy(static_cast<const float2*>(y), w, p->st[stage].total,
-                                         reinterpret_cast<double*>(p->d_state + p->red_off), kReductionParts,
-                                         d_loss, static_cast<float2*>(u), static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  return TFFT_OK;
+  return guarded("tfft_weighted_energy", [&]() -> int {
+    if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+    int rc = check_ptr(y, "y");
+    if (rc) return rc;
+    if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
+    if (!d_loss || (reinterpret_cast<uintptr_t>(d_loss) & 7)) return fail(TFFT_EINVAL, "d_loss is NULL or misaligned");
+    if (u && (rc = check_ptr(u, "u"))) return rc;
+    cudaError_t e = launch_weighted_energy(static_cast<const float2*>(y), w, p->st[stage].total,
+                                           reinterpret_cast<double*>(p->d_state + p->red_off), kReductionParts,
+                                           d_loss, static_cast<float2*>(u), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return TFFT_OK;
+  });
 }
 
 int tfft_weight_scale(tfft_plan p, int stage, const void* y, const float* w, const double* d_coef, double scale,
                       void* z, void* stream) {
-  if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
-  if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
-  int rc = check_ptr(y, "y");
-  if (rc) return rc;
-  rc = check_ptr(z, "z");
-  if (rc) return rc;
-  if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
-  cudaError_t e = launch_weight_scale(static_cast<const float2*>(y), w, d_coef, scale, p->st[stage].total,
-                                      static_cast<float2*>(z), static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
-  return TFFT_OK;
+  return guarded("tfft_weight_scale", [&]() -> int {
+    if (!p) return fail(TFFT_EINVAL, "plan is NULL");
+    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
+    int rc = check_ptr(y, "y");
+    if (rc) return rc;
+    rc = check_ptr(z, "z");
+    if (rc) return rc;
+    if (!w || (reinterpret_cast<uintptr_t>(w) & 15)) return fail(TFFT_EALIGN, "w is NULL or not 16-byte aligned");
+    cudaError_t e = launch_weight_scale(static_cast<const float2*>(y), w, d_coef, scale, p->st[stage].total,
+                                        static_cast<float2*>(z), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return TFFT_OK;
+  });
 }
 
 static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
@@ -1806,65 +1843,67 @@ int batch_launch(tfft_batch b, cudaStream_t st) {
 extern "C" {
 
 int tfft_batch_create(tfft_batch* out, int count, const tfft_plan* plans, int sign) {
-  if (!out) return fail(TFFT_EINVAL, "batch is NULL");
-  *out = nullptr;
-  if (count < 1 || !plans) return fail(TFFT_EINVAL, "need at least one plan");
-  if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
-  auto b = new tfft_batch_s();
-  b->sign = sign;
-  for (int t = 0; t < count; ++t) {
-    tfft_plan p = plans[t];
-    if (!p || !p->transformable || p->kind != TFFT_C2C || p->nelems >= (int64_t(1) << 31)) {
-      delete b;
-      return fail(TFFT_EUNSUPPORTED, "batch plans must be complex-to-complex, transformable, < 2^31 elements");
-    }
-    b->plans.push_back(p);
-    b->steps.push_back(p->steps[{sign, TFFT_MODE_FUSED}]);
-    for (const Step& s : b->steps.back()) {
-      const int kind = s.kind == S_CONTIG ? 0 : 1;
-      if ((s.kind != S_CONTIG && s.kind != S_STRIDED) || batch_candidates(kind, s.L).empty()) {
+  return guarded("tfft_batch_create", [&]() -> int {
+    if (!out) return fail(TFFT_EINVAL, "batch is NULL");
+    *out = nullptr;
+    if (count < 1 || !plans) return fail(TFFT_EINVAL, "need at least one plan");
+    if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
+    auto b = new tfft_batch_s();
+    b->sign = sign;
+    for (int t = 0; t < count; ++t) {
+      tfft_plan p = plans[t];
+      if (!p || !p->transformable || p->kind != TFFT_C2C || p->nelems >= (int64_t(1) << 31)) {
         delete b;
-        return fail(TFFT_EUNSUPPORTED, "batch: no executor tile for a pass of length " + std::to_string(s.L));
+        return fail(TFFT_EUNSUPPORTED, "batch plans must be complex-to-complex, transformable, < 2^31 elements");
       }
-      if (!b->choice.count({kind, s.L})) b->choice[{kind, s.L}] = batch_candidates(kind, s.L)[0];
+      b->plans.push_back(p);
+      b->steps.push_back(p->steps[{sign, TFFT_MODE_FUSED}]);
+      for (const Step& s : b->steps.back()) {
+        const int kind = s.kind == S_CONTIG ? 0 : 1;
+        if ((s.kind != S_CONTIG && s.kind != S_STRIDED) || batch_candidates(kind, s.L).empty()) {
+          delete b;
+          return fail(TFFT_EUNSUPPORTED, "batch: no executor tile for a pass of length " + std::to_string(s.L));
+        }
+        if (!b->choice.count({kind, s.L})) b->choice[{kind, s.L}] = batch_candidates(kind, s.L)[0];
+      }
     }
-  }
-  // segments in issue order (see batch_order); column-block capacity for the
-  // narrowest candidate
-  std::vector<std::vector<int>> idx(count);
-  size_t cb_total = 0;
-  for (const auto& tp : batch_order(b->steps)) {
-    const int t = tp.first, pass = tp.second;
-    const Step& s = b->steps[t][pass];
-    BatchSegH h;
-    h.t = t;
-    h.pass = pass;
-    h.kind = s.kind == S_CONTIG ? 0 : 1;
-    h.L = s.L;
-    h.prev = pass > 0 ? idx[t][pass - 1] : -1;
-    h.ntiles = 0;
-    h.cb_cap = 0;
-    if (h.kind == 1)
-      for (int v : batch_candidates(1, s.L)) {
-        int k, l, e, bw;
-        AxisPlan ap{};
-        batch_variant(v, k, l, e, bw, ap);
-        h.cb_cap = std::max(h.cb_cap, colblock_list(b->plans[t], s.lin, s.lout, bw).size());
-      }
-    cb_total += align_up(h.cb_cap * sizeof(int2), 256);
-    idx[t].push_back((int)b->segs.size());
-    b->segs.push_back(h);
-  }
-  b->ctr_off = 256;
-  b->seg_off = b->ctr_off + align_up(16 + b->segs.size() * sizeof(int), 256);
-  b->cb_off = b->seg_off + align_up(b->segs.size() * sizeof(BatchSeg), 256);
-  b->map_off = b->cb_off + align_up(cb_total, 256);
-  b->state_bytes = b->map_off + b->segs.size() * 2 * sizeof(CUtensorMap);
-  b->ins.assign(count, nullptr);
-  b->outs.assign(count, nullptr);
-  b->works.assign(count, nullptr);
-  *out = b;
-  return TFFT_OK;
+    // segments in issue order (see batch_order); column-block capacity for the
+    // narrowest candidate
+    std::vector<std::vector<int>> idx(count);
+    size_t cb_total = 0;
+    for (const auto& tp : batch_order(b->steps)) {
+      const int t = tp.first, pass = tp.second;
+      const Step& s = b->steps[t][pass];
+      BatchSegH h;
+      h.t = t;
+      h.pass = pass;
+      h.kind = s.kind == S_CONTIG ? 0 : 1;
+      h.L = s.L;
+      h.prev = pass > 0 ? idx[t][pass - 1] : -1;
+      h.ntiles = 0;
+      h.cb_cap = 0;
+      if (h.kind == 1)
+        for (int v : batch_candidates(1, s.L)) {
+          int k, l, e, bw;
+          AxisPlan ap{};
+          batch_variant(v, k, l, e, bw, ap);
+          h.cb_cap = std::max(h.cb_cap, colblock_list(b->plans[t], s.lin, s.lout, bw).size());
+        }
+      cb_total += align_up(h.cb_cap * sizeof(int2), 256);
+      idx[t].push_back((int)b->segs.size());
+      b->segs.push_back(h);
+    }
+    b->ctr_off = 256;
+    b->seg_off = b->ctr_off + align_up(16 + b->segs.size() * sizeof(int), 256);
+    b->cb_off = b->seg_off + align_up(b->segs.size() * sizeof(BatchSeg), 256);
+    b->map_off = b->cb_off + align_up(cb_total, 256);
+    b->state_bytes = b->map_off + b->segs.size() * 2 * sizeof(CUtensorMap);
+    b->ins.assign(count, nullptr);
+    b->outs.assign(count, nullptr);
+    b->works.assign(count, nullptr);
+    *out = b;
+    return TFFT_OK;
+  });
 }
 
 int tfft_batch_segment(tfft_batch b, int index, int* transform, int* pass) {
@@ -1889,33 +1928,37 @@ int tfft_batch_state_bytes(tfft_batch b, size_t* bytes) {
 
 int tfft_batch_bind(tfft_batch b, void* d_state, size_t bytes, const void* const* ins, void* const* outs,
                     void* const* works, void* stream) {
-  if (!b || !ins || !outs) return fail(TFFT_EINVAL, "NULL argument");
-  int rc = check_ptr(d_state, "d_state");
-  if (rc) return rc;
-  if (reinterpret_cast<uintptr_t>(d_state) & 255)
-    return fail(TFFT_EALIGN, "batch state must be 256-byte aligned (it holds tensor maps)");
-  if (bytes < b->state_bytes) return fail(TFFT_EINVAL, "batch state buffer too small");
-  const int n = (int)b->plans.size();
-  for (int t = 0; t < n; ++t) {
-    tfft_plan p = b->plans[t];
-    if (!p->d_state) return fail(TFFT_ESTATE, "every plan of the batch must be bound first");
-    if ((rc = check_ptr(ins[t], "in"))) return rc;
-    if ((rc = check_ptr(outs[t], "out"))) return rc;
-    b->ins[t] = const_cast<void*>(ins[t]);
-    b->outs[t] = outs[t];
-    b->works[t] = works ? works[t] : nullptr;
-    if (b->works[t] && (rc = check_ptr(b->works[t], "work"))) return rc;
-    b->steps[t] = p->steps[{b->sign, TFFT_MODE_FUSED}];
-    assign_buffers(b->steps[t], b->works[t] == nullptr);
-  }
-  b->d_state = static_cast<char*>(d_state);
-  return batch_upload(b, static_cast<cudaStream_t>(stream));
+  return guarded("tfft_batch_bind", [&]() -> int {
+    if (!b || !ins || !outs) return fail(TFFT_EINVAL, "NULL argument");
+    int rc = check_ptr(d_state, "d_state");
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(d_state) & 255)
+      return fail(TFFT_EALIGN, "batch state must be 256-byte aligned (it holds tensor maps)");
+    if (bytes < b->state_bytes) return fail(TFFT_EINVAL, "batch state buffer too small");
+    const int n = (int)b->plans.size();
+    for (int t = 0; t < n; ++t) {
+      tfft_plan p = b->plans[t];
+      if (!p->d_state) return fail(TFFT_ESTATE, "every plan of the batch must be bound first");
+      if ((rc = check_ptr(ins[t], "in"))) return rc;
+      if ((rc = check_ptr(outs[t], "out"))) return rc;
+      b->ins[t] = const_cast<void*>(ins[t]);
+      b->outs[t] = outs[t];
+      b->works[t] = works ? works[t] : nullptr;
+      if (b->works[t] && (rc = check_ptr(b->works[t], "work"))) return rc;
+      b->steps[t] = p->steps[{b->sign, TFFT_MODE_FUSED}];
+      assign_buffers(b->steps[t], b->works[t] == nullptr);
+    }
+    b->d_state = static_cast<char*>(d_state);
+    return batch_upload(b, static_cast<cudaStream_t>(stream));
+  });
 }
 
 int tfft_batch_execute(tfft_batch b, void* stream) {
-  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
-  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
-  return batch_launch(b, static_cast<cudaStream_t>(stream));
+  return guarded("tfft_batch_execute", [&]() -> int {
+    if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+    if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+    return batch_launch(b, static_cast<cudaStream_t>(stream));
+  });
 }
 
 int tfft_batch_num_items(tfft_batch b, int64_t* items, int* segments) {
@@ -1934,74 +1977,78 @@ int tfft_batch_variant(tfft_batch b, int kind, int L, int* variant) {
 }
 
 int tfft_batch_autotune(tfft_batch b, int reps, void* stream) {
-  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
-  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (reps < 1) reps = 3;
-  // cached choices: lines "kind L variant" in $TFFT_AUTOTUNE_CACHE
-  const char* cache = std::getenv("TFFT_AUTOTUNE_CACHE");
-  std::map<std::pair<int, int>, int> cached;
-  if (cache) {
-    if (FILE* f = std::fopen(cache, "r")) {
-      int k, l, v;
-      while (std::fscanf(f, "%d %d %d", &k, &l, &v) == 3) cached[{k, l}] = v;
-      std::fclose(f);
-    }
-  }
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return fail(TFFT_ECUDA, "cudaEventCreate");
-  int rc = TFFT_OK;
-  for (auto& kv : b->choice) {
-    const std::vector<int> cands = batch_candidates(kv.first.first, kv.first.second);
-    auto hit = cached.find(kv.first);
-    if (hit != cached.end() && std::find(cands.begin(), cands.end(), hit->second) != cands.end()) {
-      kv.second = hit->second;
-      continue;
-    }
-    if (cands.size() < 2) continue;
-    float best = 1e30f;
-    int best_v = kv.second;
-    for (int v : cands) {
-      kv.second = v;
-      if ((rc = batch_upload(b, st))) break;
-      if ((rc = batch_launch(b, st))) break;  // warm-up
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < reps && !rc; ++r) rc = batch_launch(b, st);
-      cudaEventRecord(e1, st);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        best_v = v;
+  return guarded("tfft_batch_autotune", [&]() -> int {
+    if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+    if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (reps < 1) reps = 3;
+    // cached choices: lines "kind L variant" in $TFFT_AUTOTUNE_CACHE
+    const char* cache = std::getenv("TFFT_AUTOTUNE_CACHE");
+    std::map<std::pair<int, int>, int> cached;
+    if (cache) {
+      if (FILE* f = std::fopen(cache, "r")) {
+        int k, l, v;
+        while (std::fscanf(f, "%d %d %d", &k, &l, &v) == 3) cached[{k, l}] = v;
+        std::fclose(f);
       }
     }
-    kv.second = best_v;
-    if (rc) break;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (rc) return rc;
-  if (cache) {
-    if (FILE* f = std::fopen(cache, "w")) {
-      for (auto& kv : b->choice) std::fprintf(f, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
-      std::fclose(f);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return fail(TFFT_ECUDA, "cudaEventCreate");
+    int rc = TFFT_OK;
+    for (auto& kv : b->choice) {
+      const std::vector<int> cands = batch_candidates(kv.first.first, kv.first.second);
+      auto hit = cached.find(kv.first);
+      if (hit != cached.end() && std::find(cands.begin(), cands.end(), hit->second) != cands.end()) {
+        kv.second = hit->second;
+        continue;
+      }
+      if (cands.size() < 2) continue;
+      float best = 1e30f;
+      int best_v = kv.second;
+      for (int v : cands) {
+        kv.second = v;
+        if ((rc = batch_upload(b, st))) break;
+        if ((rc = batch_launch(b, st))) break;  // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc; ++r) rc = batch_launch(b, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+          best = ms;
+          best_v = v;
+        }
+      }
+      kv.second = best_v;
+      if (rc) break;
     }
-  }
-  return batch_upload(b, st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (cache) {
+      if (FILE* f = std::fopen(cache, "w")) {
+        for (auto& kv : b->choice) std::fprintf(f, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+        std::fclose(f);
+      }
+    }
+    return batch_upload(b, st);
+  });
 }
 
 int tfft_batch_set_variant(tfft_batch b, int kind, int L, int variant, void* stream) {
-  if (!b) return fail(TFFT_EINVAL, "batch is NULL");
-  if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
-  auto it = b->choice.find({kind, L});
-  if (it == b->choice.end()) return fail(TFFT_EINVAL, "the batch has no pass of that kind and length");
-  const std::vector<int> cands = batch_candidates(kind, L);
-  if (std::find(cands.begin(), cands.end(), variant) == cands.end())
-    return fail(TFFT_EINVAL, "not a compiled variant for that kind and length");
-  it->second = variant;
-  return batch_upload(b, static_cast<cudaStream_t>(stream));
+  return guarded("tfft_batch_set_variant", [&]() -> int {
+    if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+    if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
+    auto it = b->choice.find({kind, L});
+    if (it == b->choice.end()) return fail(TFFT_EINVAL, "the batch has no pass of that kind and length");
+    const std::vector<int> cands = batch_candidates(kind, L);
+    if (std::find(cands.begin(), cands.end(), variant) == cands.end())
+      return fail(TFFT_EINVAL, "not a compiled variant for that kind and length");
+    it->second = variant;
+    return batch_upload(b, static_cast<cudaStream_t>(stream));
+  });
 }
 
 int tfft_batch_set_wait_limit(tfft_batch b, long long cycles) {
