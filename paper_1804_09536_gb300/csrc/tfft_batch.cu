@@ -316,7 +316,7 @@ constexpr size_t batch_smem() {
 #define X(ID, KIND, L, E, BW, ...)                                                                     \
   {                                                                                                    \
     const size_t v = (KIND == 0) ? (size_t)BW * line_pitch<L, __VA_ARGS__>() * sizeof(float2) \
-                                 : (size_t)L * BW * sizeof(float2) + 2 * (size_t)L * sizeof(int);     \
+                                 : strided_tile_smem<L, BW>(false);                                 \
     m = v > m ? v : m;                                                                                 \
   }
   TFFT_BATCH_VARIANTS(X)

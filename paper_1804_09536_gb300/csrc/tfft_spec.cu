@@ -24,13 +24,23 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
     contig_tile<L, E, B, false, Rs...>(a, tile, smem, opaque_tid_x(), threadIdx.y);
 }
 
+// Whether the plain strided kernel keeps the rows' part/index table for the
+// CTA's lifetime (2L words): not at 4096, where it would halve the CTAs per SM.
+__host__ __device__ constexpr bool strided_cache_rows(int L) { return L <= 2048; }
+
 template <int L, int E, int W, int... Rs>
 __global__ void __launch_bounds__(W * (L / E), min_blocks(E, W * (L / E), 1024))
     k_strided_spec(const StridedArgs a) {
   extern __shared__ float2 smem[];
   const int64_t ntiles = a.nouter * a.ncolblocks;
+  const int tid = threadIdx.y * W + threadIdx.x;
+  uint32_t* rp = nullptr;
+  if constexpr (strided_cache_rows(L)) {
+    rp = strided_rowparts<L, W>(smem);
+    strided_rowparts_init<L>(a, rp, tid, W * (L / E));  // published by the first tile's barriers
+  }
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-    strided_tile<L, E, W, false, Rs...>(a, tile, smem, threadIdx.x, opaque_tid_y(), threadIdx.y * W + threadIdx.x);
+    strided_tile<L, E, W, false, Rs...>(a, tile, smem, threadIdx.x, opaque_tid_y(), tid, rp);
 }
 
 template <class K>
@@ -57,9 +67,18 @@ cudaError_t run_strided(const StridedArgs& a, cudaStream_t s) {
   static cudaError_t attr = allow_smem(k_strided_spec<L, E, W, Rs...>);
   if (attr != cudaSuccess) return attr;
   if (a.W != W) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)L * W * sizeof(float2) + 2 * (size_t)L * sizeof(int);
+  constexpr size_t smem = strided_tile_smem<L, W>(strided_cache_rows(L));
+  // persistent: as many CTAs as fit at once, each taking every gridDim-th
+  // tile, so that the row part table is computed once per CTA
+  static const int64_t slots = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strided_spec<L, E, W, Rs...>, W * (L / E), smem);
+    return (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  }();
   int64_t grid = a.nouter * a.ncolblocks;
-  if (grid > kMaxGrid) grid = kMaxGrid;
+  if (grid > slots) grid = slots;
   if (grid < 1) return cudaSuccess;
   k_strided_spec<L, E, W, Rs...><<<(unsigned)grid, dim3(W, L / E), smem, s>>>(a);
   return cudaGetLastError();
@@ -76,10 +95,36 @@ const SpecRow kSpecs[] = {
 #undef X
 };
 
+struct StridedSpecRow {
+  int L, ES, W, nst, radix[6];
+};
+
+const StridedSpecRow kStridedSpecs[] = {
+#define X(L, ES, W, ...) {L, ES, W, (int)(sizeof((int[]){__VA_ARGS__}) / sizeof(int)), {__VA_ARGS__}},
+    TFFT_SPECS_STRIDED(X)
+#undef X
+};
+
 }  // namespace
 
 bool spec_plan(int L, bool strided, int64_t nelems, AxisPlan& ap, int& width) {
   if (nelems >= (int64_t(1) << 31)) return false;  // 32-bit row offsets
+  if (strided)
+    for (const StridedSpecRow& r : kStridedSpecs) {
+      if (r.L != L) continue;
+      ap.L = L;
+      ap.E = r.ES;
+      ap.T = L / r.ES;
+      ap.nst = r.nst;
+      ap.code = 0;
+      for (int s = 0; s < r.nst; ++s) {
+        ap.radix[s] = r.radix[s];
+        ap.code |= (uint64_t)r.radix[s] << (5 * s);
+      }
+      ap.spec = 1;
+      width = r.W;
+      return true;
+    }
   for (const SpecRow& r : kSpecs) {
     if (r.L != L) continue;
     const int E = strided ? r.ES : r.EC;
@@ -112,6 +157,10 @@ cudaError_t launch_contig_spec(const ContigArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_strided_spec(const StridedArgs& a, cudaStream_t s) {
+#define X(LL, ES, WW, ...) \
+  if (a.ap.L == LL) return a.ap.E == ES ? run_strided<LL, ES, WW, __VA_ARGS__>(a, s) : cudaErrorInvalidValue;
+  TFFT_SPECS_STRIDED(X)
+#undef X
   switch (a.ap.L) {
 #define X(L, EC, B, ES, W, ...) \
   case L:                       \

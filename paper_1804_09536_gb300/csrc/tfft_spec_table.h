@@ -29,3 +29,10 @@
   X(1024, 32, 8, 32, 8, 32, 32)             \
   X(2048, 32, 4, 32, 4, 32, 8, 8)           \
   X(4096, 16, 1, 16, 2, 16, 16, 16)
+
+// Strided passes that use other elements per thread, tile width or radices
+// than the row above for the same length: length; elements per thread; tile
+// width; radices.  512 with 16 elements (512 threads, 2 CTAs and 32 warps per
+// SM) instead of 32 (256 threads, register-limited to 16 warps per SM).
+#define TFFT_SPECS_STRIDED(X) \
+  X(512, 16, 16, 8, 8, 8)

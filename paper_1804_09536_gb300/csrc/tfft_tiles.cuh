@@ -262,24 +262,109 @@ __device__ __forceinline__ void contig_tile(const ContigArgs& a, int64_t tile, f
 
 // ------------------------------------------------------------ strided lines
 
+// Per-tile scalars of a strided tile, computed by one thread per layout and
+// shared through shared memory: the TileRows fold of the input (0) and output
+// (1) layouts, the split of the FFT axis in each (part length q, and q + 1
+// for the first r parts, Eq. decompose) and the column block.
+struct TileShared {
+  int64_t base[2], head[2], prod[2], tail[2];
+  int q[2], r[2];
+  int2 blk;
+};
+
+// Bytes of shared memory a strided tile of L x W takes: the tile, the two
+// row tables, the shared scalars and, when `cached`, the per-CTA part/index
+// table of the rows (two layouts).
+template <int L, int W>
+__host__ __device__ constexpr size_t strided_tile_smem(bool cached) {
+  return (size_t)L * W * sizeof(float2) + 2 * (size_t)L * sizeof(int) + sizeof(TileShared) +
+         (cached ? 2 * (size_t)L * sizeof(uint32_t) : 0);
+}
+
+template <int L, int W>
+__device__ __forceinline__ uint32_t* strided_rowparts(float2* smem) {
+  return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(smem) + strided_tile_smem<L, W>(false));
+}
+
+// Part c and index l (packed c << 16 | l) of every row i < L along the FFT
+// axis, input layout in [0, L), output layout in [L, 2L): they depend on the
+// axis split only, so a persistent CTA computes them once.
+template <int L>
+__device__ __forceinline__ void strided_rowparts_init(const StridedArgs& a, uint32_t* rp, int tid, int nthreads) {
+  for (int i = tid; i < 2 * L; i += nthreads) {
+    const int row = i < L ? i : i - L;
+    const int64_t N = i < L ? a.lin.N[a.axis] : a.lout.N[a.axis];
+    const int64_t M = i < L ? a.lin.Mx[a.axis] : a.lout.Mx[a.axis];
+    int64_t c = 0, l = row, n = N;
+    if (M > 1) locate(N, M, row, c, l, n);
+    rp[i] = ((uint32_t)c << 16) | (uint32_t)l;
+  }
+}
+
+// The fold of one layout for tile position tp, written to ts slot `k`.
+__device__ __forceinline__ void tile_fold(const StridedArgs& a, const DevLayout& lay, const StridedTilePos& tp,
+                                          TileShared* ts, int k) {
+  const TileRows tr(a, lay, tp);
+  ts->base[k] = tr.base;
+  ts->head[k] = tr.head;
+  ts->prod[k] = tr.prod;
+  ts->tail[k] = tr.tail;
+  const uint32_t N = (uint32_t)tr.N, M = (uint32_t)tr.M;
+  ts->q[k] = (int)(N / M);
+  ts->r[k] = (int)(N - (N / M) * M);
+}
+
+// Element offset of row i of a layout from the shared fold (slot k): the
+// part's offset plus the C-order index inside it.
+__device__ __forceinline__ int row_offset(const DevLayout& lay, int axis, const TileShared* ts, int k, int64_t c,
+                                          int64_t l) {
+  const int64_t n = ts->q[k] + (c < ts->r[k] ? 1 : 0);
+  return (int)(lay.offset[ts->base[k] + c * lay.rs[axis]] + (ts->head[k] * n + l) * ts->prod[k] + ts->tail[k]);
+}
+
 // One strided tile (outer index and column block `tile`): thread jt of
-// column cx; tid = thread index in the CTA (W x T threads).
+// column cx; tid = thread index in the CTA (W x T threads).  `rp` is the
+// per-CTA part/index table of strided_rowparts_init, or null (then each row
+// locates its part itself).
 template <int L, int E, int W, bool CG, int... Rs>
 __device__ __forceinline__ void strided_tile(const StridedArgs& a, int64_t tile, float2* smem, int cx, int jt,
-                                             int tid) {
+                                             int tid, const uint32_t* rp = nullptr) {
   constexpr int T = L / E, NST = sizeof...(Rs);
+  static_assert(W * T > 32, "the two layouts' folds are computed by threads 0 and 32");
   int* rin = reinterpret_cast<int*>(smem + L * W);
   int* rout = rin + L;
+  TileShared* ts = reinterpret_cast<TileShared*>(rout + L);
   const bool inv = a.sign > 0;
-  const StridedTilePos tp(a, tile);
-  const TileRows ri(a, a.lin, tp), ro(a, a.lout, tp);
-  __syncthreads();  // the previous tile is done with the row tables
-  for (int i = tid; i < L; i += W * T) {
-    rin[i] = (int)ri.row(a.lin, i);
-    rout[i] = (int)ro.row(a.lout, i);
+  __syncthreads();  // the previous tile is done with the row tables and the scalars
+  if (tid == 0) {
+    const StridedTilePos tp(a, tile);
+    tile_fold(a, a.lin, tp, ts, 0);
+    ts->blk = tp.blk;
+  } else if (tid == 32) {
+    const StridedTilePos tp(a, tile);
+    tile_fold(a, a.lout, tp, ts, 1);
   }
   __syncthreads();
-  const int2 blk = tp.blk;
+  for (int i = tid; i < 2 * L; i += W * T) {
+    const bool out = i >= L;
+    const int row = out ? i - L : i;
+    int64_t c = 0, l = row;
+    if (rp != nullptr) {
+      c = rp[i] >> 16;
+      l = rp[i] & 0xFFFF;
+    } else {
+      int64_t n;
+      const int64_t N = out ? a.lout.N[a.axis] : a.lin.N[a.axis];
+      const int64_t M = out ? a.lout.Mx[a.axis] : a.lin.Mx[a.axis];
+      if (M > 1) locate(N, M, row, c, l, n);
+    }
+    if (out)
+      rout[row] = row_offset(a.lout, a.axis, ts, 1, c, l);
+    else
+      rin[row] = row_offset(a.lin, a.axis, ts, 0, c, l);
+  }
+  __syncthreads();
+  const int2 blk = ts->blk;
   const bool act = cx < blk.y;
   float2 v[emax<L, E, Rs...>()];
   static_for<0, NST>([&](auto S) {

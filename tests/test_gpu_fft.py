@@ -88,9 +88,13 @@ def test_forward_inverse_vs_oracle(cuda_device, shape, grid):
 @pytest.mark.parametrize("shape,grid", [((256, 128, 256), (2, 4)), ((512, 64, 64), (4, 2)),
                                         ((64, 64, 64), (2, 2)), ((128, 512, 64), (2, 2)),
                                         ((384, 32, 64), (2, 4)), ((1024, 16, 32), (2, 2))])
-def test_tma_and_plain_passes_identical(cuda_device, shape, grid):
-    """The TMA-staged passes and the plain load/store passes run the same
-    butterflies on every line: forward and inverse outputs are bit-identical."""
+def test_tma_and_plain_passes_agree(cuda_device, shape, grid):
+    """The TMA-staged passes and the plain load/store passes move every line
+    the same way.  Where both run the same radices the outputs are
+    bit-identical; the plain 512-long strided pass runs 8 x 8 x 8 (16 values
+    per thread, twice the resident warps) where the TMA kernel runs 32 x 16,
+    so there the two agree to rounding (a misplaced line or element would
+    show as an error of order 1e-3 or more)."""
     from paper_1804_09536_gb300.plan import Plan
     x = inputs.normal_complex(shape, seed=7).numpy()
     b0 = R.scatter(x, grid, 0)
@@ -105,8 +109,12 @@ def test_tma_and_plain_passes_identical(cuda_device, shape, grid):
     zp = pp.inverse(yp.clone())
     torch.cuda.synchronize()
     assert pt.device_status() == 0
-    assert np.array_equal(bits(yt), bits(yp))
-    assert np.array_equal(bits(zt), bits(zp))
+    if 512 not in shape[:-1]:
+        assert np.array_equal(bits(yt), bits(yp))
+        assert np.array_equal(bits(zt), bits(zp))
+    else:
+        assert rel_l2(yt.cpu().numpy(), yp.cpu().numpy()) <= 2e-6
+        assert rel_l2(zt.cpu().numpy(), zp.cpu().numpy()) <= 2e-6
     want = dft.distributed_forward(b0.astype(np.complex128), shape, grid)
     assert rel_l2(yt.cpu().numpy(), want) <= RTOL_FP32
 
