@@ -23,7 +23,7 @@ using namespace tiles;
 // parts of X[0] and X[L] are ignored (taken as zero).
 
 template <int L, int E, int B, int... Rs>
-__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
+__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
     k_r2c_spec(const RealArgs a) {
   constexpr int T = L / E, NST = sizeof...(Rs);
   constexpr int LP = line_pitch<L, Rs...>();
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
 }
 
 template <int L, int E, int B, int... Rs>
-__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 512))
+__global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
     k_c2r_spec(const RealArgs a) {
   constexpr int T = L / E, NST = sizeof...(Rs);
   constexpr int LP = line_pitch<L, Rs...>() + 1;
