@@ -95,6 +95,16 @@ const SpecRow kSpecs[] = {
 #undef X
 };
 
+// Whether TFFT_SPECS_STRIDED replaces the strided kernel of TFFT_SPECS for L
+// (the replaced one is then not instantiated).
+constexpr bool strided_overridden(int L) {
+#define X(LL, ...) \
+  if (L == LL) return true;
+  TFFT_SPECS_STRIDED(X)
+#undef X
+  return false;
+}
+
 struct StridedSpecRow {
   int L, ES, W, nst, radix[6];
 };
@@ -162,9 +172,10 @@ cudaError_t launch_strided_spec(const StridedArgs& a, cudaStream_t s) {
   TFFT_SPECS_STRIDED(X)
 #undef X
   switch (a.ap.L) {
-#define X(L, EC, B, ES, W, ...) \
-  case L:                       \
-    return run_strided<L, ES, W, __VA_ARGS__>(a, s);
+#define X(L, EC, B, ES, W, ...)                                          \
+  case L:                                                                \
+    if constexpr (!strided_overridden(L)) return run_strided<L, ES, W, __VA_ARGS__>(a, s); \
+    return cudaErrorInvalidValue;
     TFFT_SPECS(X)
 #undef X
     default:

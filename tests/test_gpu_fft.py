@@ -46,6 +46,7 @@ CASES = [
     ((42, 127, 256), (3, 4)),        # the paper's App. A shape: 42 = 2.3.7 and 127 (prime) by Bluestein
     ((7, 11, 26), (2, 3)),           # Bluestein on every axis (26 = 2.13), uneven blocks
     ((2047,), ()),                   # the longest Bluestein line (convolution length 4096)
+    ((16, 17, 18, 19), (2, 3, 2)),   # App. B's 4-D shape on a 3-D grid (17, 19 by Bluestein)
 ]
 
 
