@@ -47,6 +47,7 @@ CASES = [
     ((7, 11, 26), (2, 3)),           # Bluestein on every axis (26 = 2.13), uneven blocks
     ((2047,), ()),                   # the longest Bluestein line (convolution length 4096)
     ((16, 17, 18, 19), (2, 3, 2)),   # App. B's 4-D shape on a 3-D grid (17, 19 by Bluestein)
+    ((32, 32, 64), (48, 2)),         # more parts than rows on both specialised strided axes (empty parts)
 ]
 
 
