@@ -366,7 +366,17 @@ def profile_workload(args, dev):
     import torch
     from paper_1804_09536_gb300 import inputs
     from paper_1804_09536_gb300.plan import Batch, Plan
-    if args.profile_workload == "batch":
+    if args.profile_workload == "r2c":
+        plan = Plan(SHAPE, GRID, kind="r2c", device=dev)
+        xr = plan.scatter(inputs.normal_real(SHAPE, seed=0).to(dev), 0, real=True)
+        yc = plan.empty_stage(plan.g)
+        zr = plan.empty_stage(0, real=True)
+        work = plan.workspace("fused")
+
+        def one():
+            plan.execute(-1, xr, yc, "fused", work)
+            plan.execute(1, yc, zr, "fused", work)
+    elif args.profile_workload == "batch":
         problems = inputs.batch_problems(48, seed=0)[:args.batch_count]
         plans = [Plan(sh, gr, device=dev) for sh, gr in problems]
         b = Batch(plans, sign=-1)
@@ -707,10 +717,11 @@ def main():
                     help="headline loop only (no comparison paths, e2e or CPU baseline)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "fp16x3"],
                     help="arithmetic of the length-512 contiguous passes in the headline loop")
-    ap.add_argument("--profile-workload", default="fft", choices=["fft", "batch", "loss"],
+    ap.add_argument("--profile-workload", default="fft", choices=["fft", "batch", "loss", "r2c"],
                     help="with --profile-only: the loop to run (fft: the headline step; batch: the "
                          "batch executor over the first --batch-count transforms; loss: the "
-                         "loss + gradient step)")
+                         "loss + gradient step; r2c: real-to-complex forward + complex-to-real "
+                         "inverse of --shape on --grid)")
     ap.add_argument("--batch-count", type=int, default=48)
     args = ap.parse_args()
     if args.precision != "fp32" and not args.profile_only:
