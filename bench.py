@@ -665,11 +665,38 @@ def cpu_baseline(target_s: float = 15.0):
     secs = _oracle_sample(x, k)
     frac = k / SHAPE[0]
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": round(frac * FLOP_PER_STEP / secs / 1e9, 4), "unit": UNIT, "cores": cores,
-            "kind": "oracle",
-            "sample": f"oracle FP64 exact-angle DFT matrices, forward+inverse along all 3 axes over "
-                      f"{k} of 512 slices ({frac:.4f} of one 512^3 step's lines, {secs:.1f} s), "
-                      f"5NlogN-equivalent flops; redistribution copies not included"}
+    out = {"value": round(frac * FLOP_PER_STEP / secs / 1e9, 4), "unit": UNIT, "cores": cores,
+           "kind": "oracle",
+           "sample": f"oracle FP64 exact-angle DFT matrices, forward+inverse along all 3 axes over "
+                     f"{k} of {SHAPE[0]} slices ({frac:.4f} of one step's lines, {secs:.1f} s), "
+                     f"5NlogN-equivalent flops; redistribution copies timed separately"}
+    # the oracle's index-level redistribution (Alg. 3 subarray copies), one exchange
+    # of the whole stage buffer
+    from oracle import redistribute
+    buf = redistribute.scatter(x, GRID, 0)
+    t = time.perf_counter()
+    _ = redistribute.exchange_subarray(buf, SHAPE, GRID, 0, 1)
+    tr = time.perf_counter() - t
+    out["redistribution"] = {"ms": round(tr * 1e3, 1), "GBps": round(2 * buf.nbytes / tr / 1e9, 2),
+                             "sample": "oracle exchange_subarray, stage 0 -> 1 of the whole "
+                                       f"{'x'.join(map(str, SHAPE))} complex64 buffer (read + write)"}
+    del buf, _
+    # context, not the oracle: a library CPU FFT on the same input and cores
+    try:
+        import scipy.fft
+        scipy.fft.ifftn(scipy.fft.fftn(x[:8], workers=cores, norm="forward"), workers=cores, norm="forward")
+        t = time.perf_counter()
+        y = scipy.fft.fftn(x, workers=cores, norm="forward")
+        z = scipy.fft.ifftn(y, workers=cores, norm="forward")
+        tl = time.perf_counter() - t
+        del y, z
+        out["library_context"] = {"value": round(FLOP_PER_STEP / tl / 1e9, 2), "unit": UNIT,
+                                  "ms_per_step": round(tl * 1e3, 1),
+                                  "sample": f"scipy.fft.fftn + ifftn (pocketfft, complex64, workers={cores}) "
+                                            "of the whole array, one step; a library, not the oracle"}
+    except ImportError:
+        pass
+    return out
 
 
 def run_reference(args):
@@ -687,7 +714,7 @@ def run_reference(args):
     value = frac * FLOP_PER_STEP / secs / 1e9
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     sample = (f"oracle FP64 exact-angle DFT matrices, forward+inverse along all 3 axes over {k} of "
-              f"512 slices per step ({frac:.4f} of the step's lines)")
+              f"{SHAPE[0]} slices per step ({frac:.4f} of the step's lines)")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(secs * 1e3 / frac, 3), "higher_is_better": True, "scaling": "weak",
