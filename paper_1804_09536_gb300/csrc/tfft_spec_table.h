@@ -33,6 +33,9 @@
 // Strided passes that use other elements per thread, tile width or radices
 // than the row above for the same length: length; elements per thread; tile
 // width; radices.  512 with 16 elements (512 threads, 2 CTAs and 32 warps per
-// SM) instead of 32 (256 threads, register-limited to 16 warps per SM).
+// SM) instead of 32 (256 threads, register-limited to 16 warps per SM); 256
+// in 16-column tiles (256 threads, 4 CTAs per SM) instead of 32 (512 threads,
+// 2 CTAs): the same warps per SM in more, independent CTAs.
 #define TFFT_SPECS_STRIDED(X) \
-  X(512, 16, 16, 8, 8, 8)
+  X(512, 16, 16, 8, 8, 8)           \
+  X(256, 16, 16, 16, 16)
