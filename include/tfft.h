@@ -146,7 +146,11 @@ int tfft_plan_local_box(tfft_plan plan, int stage, int real, int rank, int64_t *
  * bytes of device memory and passes it to tfft_plan_bind(), which uploads the
  * tables and generates the twiddle factors on the device in double precision
  * (then rounds them to float).  The state must stay allocated and unmodified
- * while the plan is used; bind again after moving it.
+ * while the plan is used; bind again after moving it.  Binding records the
+ * current device: every later call that launches work on the plan (execute,
+ * adjoint, redistribute, partial, the loss calls, host transforms, the
+ * device status read) requires that device to be current and otherwise
+ * returns TFFT_EINVAL without launching.
  */
 int tfft_plan_state_bytes(tfft_plan plan, size_t *bytes);
 int tfft_plan_bind(tfft_plan plan, void *d_state, size_t bytes, void *stream);
@@ -237,7 +241,8 @@ int tfft_execute_host(tfft_plan plan, int nsigns, const int *signs, int count, c
  * the rest in double, in a fixed order (deterministic); the sum is written to
  * d_loss[0] (device memory).  When u is not NULL the same sweep writes
  * u = w^2 y (complex64, same layout; u may alias y): the gradient of
- * g * loss(F x) is then tfft_adjoint(u) with d_coef = 2 g.  Uses scratch
+ * g * loss(F x) is then tfft_weighted_energy_grad(u, d_g = &g), i.e.
+ * tfft_adjoint(u) with d_coef = 2 g.  Uses scratch
  * inside the plan state: calls on one plan must not overlap on the GPU.
  */
 int tfft_weighted_energy(tfft_plan plan, int stage, const void *y, const float *w, double *d_loss,
@@ -252,6 +257,19 @@ int tfft_weighted_energy(tfft_plan plan, int stage, const void *y, const float *
 int tfft_weight_scale(tfft_plan plan, int stage, const void *y, const float *w, const double *d_coef,
                       double scale, void *z, void *stream);
 
+/*
+ * Gradient of g * loss(F x) for the loss of tfft_weighted_energy():
+ * 2 g F^H(u), u = w^2 F(x) as that call wrote it (stage g), result in stage
+ * 0 (d/dRe x + i d/dIm x convention; the chain rule of Sec. 2's linear map
+ * F, whose adjoint is tfft_adjoint).  The factor 2 is applied with the
+ * adjoint's own 1/N on its last pass, g is read there on the device from
+ * d_g (device memory, 8-byte aligned; NULL means g = 1), so the factor costs
+ * no sweep and no host synchronisation.  Complex-to-complex plans; other
+ * arguments as tfft_adjoint().
+ */
+int tfft_weighted_energy_grad(tfft_plan plan, int mode, const void *u, void *out, void *work,
+                              size_t work_bytes, const double *d_g, void *stream);
+
 /* Number of kernel launches tfft_execute() makes in a mode and direction. */
 int tfft_plan_num_launches(tfft_plan plan, int sign, int mode, int *nlaunches);
 
@@ -265,10 +283,29 @@ int tfft_plan_launch_info(tfft_plan plan, int sign, int mode, int index, char *n
                           int name_len, int64_t *bytes);
 
 /*
- * Device status word of the plan's state buffer: bit 0 (value 1) is set when
- * a kernel gave up on a bounded wait for one of its own asynchronous copies
- * (nothing else writes it).  Synchronises `stream`; reset != 0 clears the
- * word afterwards.
+ * The copy tasks of launch `index` of tfft_execute() in a direction and mode
+ * when that launch is a subarray box copy (Alg. 3's exchange, or the pack,
+ * all-to-all copy and unpack of TFFT_MODE_PACKED): task t copies nrows rows
+ * of rowlen contiguous complex64 elements, row r from in[src + r ss] to
+ * out[dst + r ds] (element offsets into the launch's input and output
+ * buffers).  Writes min(max_tasks, count) tasks as 6 int64 values each
+ * (src, dst, ss, ds, nrows, rowlen) to `tasks` (host memory, may be NULL
+ * when max_tasks is 0) and the count to *ntasks.  Host only; TFFT_EINVAL if
+ * the launch is not a box copy.  For inspection and tests of the planner.
+ */
+int tfft_plan_copy_tasks(tfft_plan plan, int sign, int mode, int index, int64_t *tasks, int64_t max_tasks,
+                         int64_t *ntasks);
+
+/*
+ * Device status word of the plan's state buffer (nothing else writes it):
+ * bit 0 (value 1) is set when a kernel gave up on a bounded wait for one of
+ * its own asynchronous copies or tensor-core operations (the kernel then
+ * stops and its output is incomplete); bit 1 (2) when a TMA tile buffer was
+ * not 128-byte aligned (the copy was skipped); bit 2 (4) when, after such a
+ * give-up, tensor-core operations were still running at the end of a
+ * bounded clean-up wait, so the CTA left its tensor memory allocated rather
+ * than release memory still being written.  Synchronises `stream`;
+ * reset != 0 clears the word afterwards.
  */
 int tfft_plan_device_status(tfft_plan plan, int *status, int reset, void *stream);
 
@@ -350,19 +387,23 @@ int tfft_batch_device_status(tfft_batch batch, int *status, int reset, void *str
  * allocator, where an extra cudaMalloc is forbidden or finds no memory.  The
  * paper has no counterpart; it is an interface convenience.
  *
- * Same result as tfft_execute(plan, sign, TFFT_MODE_FUSED, in, out, work, ...)
- * with a caller-allocated workspace: the input is kept.  Nothing is
+ * Same result, bit for bit, as tfft_execute(plan, sign, TFFT_MODE_FUSED, in,
+ * out, work, ...) with a caller-allocated workspace: the input is kept --
+ * except by the complex-to-real backward of a TFFT_R2C plan (sign +1), which
+ * uses its input as scratch here too and leaves it undefined.  Nothing is
  * allocated: the scratch is a static __device__ array of
  * TFFT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
  * holds until the process exits; a plan whose stage buffer is larger is
- * rejected with TFFT_EWORKSPACE (message in tfft_last_error()).
+ * rejected with TFFT_EWORKSPACE (message in tfft_last_error()).  The current
+ * device must be the one the plan was bound on (else TFFT_EINVAL).
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * last call's contents (every call overwrites what it reads, so nothing has
- * to start at zero); calls whose work overlaps on the GPU -- on different
- * streams, or from different threads -- race on it.
+ * Every call looks up the array's device address (cudaGetSymbolAddress, with
+ * the plan's device current); the first call on a device also loads the
+ * library's module there, so make that first call before any stream capture.
+ * All calls and all plans share the one array and it keeps the last call's
+ * contents (every call overwrites what it reads, so nothing has to start at
+ * zero); calls whose work overlaps on the GPU -- on different streams, or
+ * from different threads -- race on it.
  */
 #define TFFT_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 int tfft_execute_noalloc(tfft_plan plan, int sign, const void *in, void *out, void *stream);

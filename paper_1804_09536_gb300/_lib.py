@@ -57,6 +57,7 @@ SIGNATURES = {
     "tfft_plan_set_launch_events": [_vp, ctypes.POINTER(_vp), ctypes.c_int],
     "tfft_adjoint": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp, _vp],
     "tfft_weighted_energy": [_vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp],
+    "tfft_weighted_energy_grad": [_vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp, _vp],
     "tfft_host_space_bytes": [_vp, ctypes.POINTER(ctypes.c_size_t)],
     "tfft_execute_host": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(_vp),
                           ctypes.POINTER(_vp), _vp, ctypes.c_size_t, _vp],
@@ -77,6 +78,7 @@ SIGNATURES = {
     "tfft_batch_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],
     "tfft_execute_noalloc": [_vp, ctypes.c_int, _vp, _vp, _vp],
     "tfft_plan_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],
+    "tfft_plan_copy_tasks": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int64, _i64p],
     "tfft_plan_launch_info": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
                               ctypes.c_int, _i64p],
 }

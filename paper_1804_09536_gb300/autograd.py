@@ -4,10 +4,11 @@ loss(x) = sum_k |F(x)_k w_k|^2, F the plan's forward transform (stage 0 ->
 stage g, paper normalisation).  Backward: d loss / d x = 2 F^H (w^2 F x)
 (d/dRe + i d/dIm convention used by torch for complex inputs).  The forward
 sweep that sums the loss also writes u = w^2 y over y (one pass over y and w);
-the backward is the adjoint transform of u (tfft_adjoint: the backward passes
-with the redistributions reversed and 1/N) with the factor 2 g applied on the
-device by its last pass, so the gradient seed is never materialised.  Every
-step runs in the library's kernels.
+the backward is tfft_weighted_energy_grad: the adjoint transform of u (the
+backward passes with the redistributions reversed and 1/N) whose last pass
+also applies the factor 2 and the upstream gradient g, read on the device, so
+the gradient seed is never materialised.  Every step, the factor 2 included,
+runs in the library's kernels; torch only hands over g's device pointer.
 """
 from __future__ import annotations
 
@@ -27,8 +28,10 @@ class SpectralWeightLoss(torch.autograd.Function):
     def backward(ctx, gout: torch.Tensor):
         (u,) = ctx.saved_tensors
         plan = ctx.plan
-        c = (2.0 * gout.detach().to(torch.float64)).reshape(()).contiguous()
-        gx = plan.adjoint(u, coef=c)  # 2 g F^H (w^2 y); u kept (a retained graph may run it again)
+        if gout.dtype != torch.float64:
+            raise TypeError("the loss is float64, so is its upstream gradient")
+        g = gout.detach().reshape(()).contiguous()  # a view of the same device scalar
+        gx = plan.weighted_energy_grad(u, g)  # 2 g F^H (w^2 y); u kept (a retained graph may run it again)
         return gx, None, None
 
 

@@ -405,24 +405,22 @@ int batch_num_variants() {
 }
 
 cudaError_t launch_batch(const BatchArgs& b, int grid, cudaStream_t s) {
-  static cudaError_t attr = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)batch_smem());
+  static PerDevice<cudaError_t> attr_cache;
+  const cudaError_t attr = smem_attr_once(attr_cache, k_batch, (int)batch_smem());
   if (attr != cudaSuccess) return attr;
   k_batch<<<grid, kBatchThreads, batch_smem(), s>>>(b);
   return cudaGetLastError();
 }
 
 int batch_grid() {
-  static int g = [] {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static PerDevice<int> cache;
+  return cache.get(current_device(), [] {
+    int per = 0;
     cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kBatchThreads, batch_smem());
     if (per < 1) per = 1;
-    return (sms > 0 ? sms : 1) * per;
-  }();
-  return g;
+    return device_sm_count() * per;
+  });
 }
 
 }  // namespace tfft

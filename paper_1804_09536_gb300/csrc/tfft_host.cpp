@@ -72,11 +72,11 @@ struct Step {
   bool scaled = false;
   double scale_value = 1.0;
   const double* coef = nullptr;  // device factor on a contiguous pass's output (one call only)
-  // box copies
+  // box copies: the copy tasks of the step's box list
   size_t box_off = 0;
-  int nboxes = 0;
-  int64_t max_rows = 0;
+  int64_t ntasks = 0;
   int vec2 = 0;
+  int64_t box_elems = 0;
   // TMA-staged strided pass: variant, its column blocks and the tile
   // geometry of the input and output layouts
   bool tma = false;
@@ -90,6 +90,15 @@ struct Step {
 struct ExchangeBoxes {  // one adjacent-stage exchange
   std::vector<BoxDesc> direct, pack, xchg, unpack;
   bool pack_identity = false, unpack_identity = false;
+};
+
+// A box list as the copy kernel runs it: offset of its task table in the
+// plan state, task count, whether 16-byte copies apply, elements copied.
+struct BoxList {
+  size_t off = 0;
+  int64_t ntasks = 0;
+  int vec2 = 1;
+  int64_t elems = 0;
 };
 
 }  // namespace
@@ -123,11 +132,12 @@ struct tfft_plan_s {
   std::map<int, BlueH> blue;
   std::map<std::tuple<int, int, int>, std::pair<size_t, int64_t>> colblocks;  // (lin,lout,W)
   std::map<std::pair<int, int>, ExchangeBoxes> xboxes;                       // (from,to)
-  std::map<std::pair<int, int>, std::vector<size_t>> xbox_off;  // direct, pack, xchg, unpack
+  std::map<std::pair<int, int>, std::vector<BoxList>> xbox_off;  // direct, pack, xchg, unpack
   std::map<std::pair<int, int>, std::vector<Step>> steps;        // (sign, mode)
   std::vector<uint8_t> image;
   size_t state_bytes = 0;
   char* d_state = nullptr;
+  int device = -1;  // device the state was bound on
   std::vector<cudaEvent_t> events;
   // copy streams and events of tfft_execute_host (created on first use)
   struct HostIo {
@@ -411,6 +421,98 @@ void add_flat(std::vector<BoxDesc>& out, int64_t src, int64_t dst, int64_t n) {
   }
 }
 
+// Copy tasks of a box list.  Each box first loses its unit dimensions and
+// merges every pair of neighbouring dimensions that is contiguous on both
+// sides (outer stride = inner stride x inner extent); the innermost run is
+// then one row.  A run longer than kRowMax elements becomes rows of kRowChunk
+// (plus a tail row); otherwise the next dimension out supplies the rows.
+// Rows are grouped into tasks of about kTaskElems elements, and every other
+// dimension is enumerated on the host.
+constexpr int64_t kRowMax = 4096, kRowChunk = 2048, kTaskElems = 16384;
+
+void box_tasks(const BoxDesc& b, std::vector<CopyTask>& out) {
+  struct Dim {
+    int64_t e, s, d;
+  };
+  std::vector<Dim> dims;
+  for (int m = 0; m < MAXD; ++m)
+    if (b.ext[m] != 1) dims.push_back({b.ext[m], b.ss[m], b.ds[m]});
+  for (const Dim& x : dims)
+    if (x.e <= 0) return;  // empty box
+  if (dims.empty()) dims.push_back({1, 1, 1});
+  for (size_t k = dims.size() - 1; k > 0; --k) {  // merge contiguous neighbours, innermost first
+    Dim& in = dims[k];
+    const Dim& o = dims[k - 1];
+    if (o.s == in.s * in.e && o.d == in.d * in.e) {
+      in.e *= o.e;
+      dims.erase(dims.begin() + (long)(k - 1));
+    }
+  }
+  // innermost run (stride 1 on both sides; a unit-extent innermost axis
+  // leaves a strided last dimension, whose elements are then rows of one)
+  if (dims.back().s != 1 || dims.back().d != 1) dims.push_back({1, 1, 1});
+  const Dim run = dims.back();
+  dims.pop_back();
+  std::vector<Dim> outer = dims;  // enumerated on the host
+  int64_t rows = 1, rs = 0, rd = 0, rowlen = run.e, tail = 0;
+  if (run.e > kRowMax) {
+    rowlen = kRowChunk;
+    rows = run.e / kRowChunk;
+    tail = run.e - rows * kRowChunk;
+    rs = rd = kRowChunk;
+  } else if (!outer.empty()) {
+    rows = outer.back().e;
+    rs = outer.back().s;
+    rd = outer.back().d;
+    outer.pop_back();
+  }
+  const int64_t rows_per_task = std::max<int64_t>(1, kTaskElems / std::max<int64_t>(1, rowlen));
+  int64_t count = 1;
+  for (const Dim& x : outer) count *= x.e;
+  for (int64_t idx = 0; idx < count; ++idx) {
+    int64_t so = b.src, dof = b.dst, r = idx;
+    for (size_t k = outer.size(); k-- > 0;) {
+      const int64_t i = r % outer[k].e;
+      r /= outer[k].e;
+      so += i * outer[k].s;
+      dof += i * outer[k].d;
+    }
+    for (int64_t r0 = 0; r0 < rows; r0 += rows_per_task) {
+      CopyTask t;
+      t.src = so + r0 * rs;
+      t.dst = dof + r0 * rd;
+      t.ss = rs;
+      t.ds = rd;
+      t.nrows = (int32_t)std::min(rows_per_task, rows - r0);
+      t.rowlen = (int32_t)rowlen;
+      out.push_back(t);
+    }
+    if (tail > 0) {
+      CopyTask t;
+      t.src = so + rows * kRowChunk;
+      t.dst = dof + rows * kRowChunk;
+      t.ss = t.ds = tail;
+      t.nrows = 1;
+      t.rowlen = (int32_t)tail;
+      out.push_back(t);
+    }
+  }
+}
+
+BoxList add_box_list(tfft_plan p, const std::vector<BoxDesc>& boxes) {
+  std::vector<CopyTask> tasks;
+  BoxList L;
+  for (const BoxDesc& b : boxes) {
+    box_tasks(b, tasks);
+    L.elems += b.ext[0] * b.ext[1] * b.ext[2] * b.ext[3];
+  }
+  for (const CopyTask& t : tasks)
+    if ((t.src | t.dst | t.ss | t.ds | (int64_t)t.rowlen) & 1) L.vec2 = 0;
+  L.ntasks = (int64_t)tasks.size();
+  L.off = image_add(p, tasks.data(), tasks.size() * sizeof(CopyTask));
+  return L;
+}
+
 bool box_contiguous(const BoxDesc& b, const int64_t* st) {
   int64_t rm[MAXD];
   row_major_strides(MAXD, b.ext, rm);
@@ -507,27 +609,20 @@ void build_exchange(tfft_plan p, int s_from, int s_to) {
       recv += cnt;
     }
   }
-  std::vector<size_t> offs;
-  for (auto* vec : {&X.direct, &X.pack, &X.xchg, &X.unpack})
-    offs.push_back(image_add(p, vec->data(), vec->size() * sizeof(BoxDesc)));
+  std::vector<BoxList> offs;
+  for (auto* vec : {&X.direct, &X.pack, &X.xchg, &X.unpack}) offs.push_back(add_box_list(p, *vec));
   p->xboxes[{s_from, s_to}] = std::move(X);
   p->xbox_off[{s_from, s_to}] = offs;
 }
 
-Step box_step(tfft_plan p, const std::vector<BoxDesc>& boxes, size_t off) {
+Step box_step(const BoxList& L) {
   Step s;
   s.kind = S_BOX;
   s.inplace_ok = false;
-  s.box_off = off;
-  s.nboxes = (int)boxes.size();
-  s.vec2 = 1;
-  for (const BoxDesc& b : boxes) {
-    s.max_rows = std::max<int64_t>(s.max_rows, b.ext[0] * b.ext[1] * b.ext[2]);
-    if ((b.src | b.dst | b.ext[3]) & 1) s.vec2 = 0;
-    for (int m = 0; m < MAXD; ++m)
-      if ((b.ss[m] | b.ds[m]) & 1) s.vec2 = 0;
-  }
-  (void)p;
+  s.box_off = L.off;
+  s.ntasks = L.ntasks;
+  s.vec2 = L.vec2;
+  s.box_elems = L.elems;
   return s;
 }
 
@@ -711,13 +806,13 @@ Step last_axis_step(tfft_plan p, int sign) {
 
 void add_exchange_steps(tfft_plan p, std::vector<Step>& out, int from, int to, int mode) {
   const ExchangeBoxes& X = p->xboxes[{from, to}];
-  const std::vector<size_t>& off = p->xbox_off[{from, to}];
+  const std::vector<BoxList>& off = p->xbox_off[{from, to}];
   if (mode == TFFT_MODE_UNFUSED) {
-    out.push_back(box_step(p, X.direct, off[0]));
+    out.push_back(box_step(off[0]));
   } else {
-    if (!X.pack_identity) out.push_back(box_step(p, X.pack, off[1]));
-    out.push_back(box_step(p, X.xchg, off[2]));
-    if (!X.unpack_identity) out.push_back(box_step(p, X.unpack, off[3]));
+    if (!X.pack_identity) out.push_back(box_step(off[1]));
+    out.push_back(box_step(off[2]));
+    if (!X.unpack_identity) out.push_back(box_step(off[3]));
   }
 }
 
@@ -794,6 +889,17 @@ int check_ptr(const void* ptr, const char* name) {
   if (!ptr) return fail(TFFT_EINVAL, std::string(name) + " is NULL");
   if (reinterpret_cast<uintptr_t>(ptr) & 15)
     return fail(TFFT_EALIGN, std::string(name) + " is not 16-byte aligned");
+  return TFFT_OK;
+}
+
+// The plan is bound, and the calling thread's current device is the one it
+// was bound on (its state, twiddles and tensor maps live there).
+int check_bound(tfft_plan p) {
+  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  const int dev = current_device();
+  if (dev != p->device)
+    return fail(TFFT_EINVAL, "the current device (" + std::to_string(dev) + ") is not the device the plan was bound on (" +
+                                 std::to_string(p->device) + ")");
   return TFFT_OK;
 }
 
@@ -888,10 +994,10 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     BoxArgs a;
     a.in = in;
     a.out = out;
-    a.boxes = reinterpret_cast<const BoxDesc*>(p->d_state + s.box_off);
-    a.nboxes = s.nboxes;
+    a.tasks = reinterpret_cast<const CopyTask*>(p->d_state + s.box_off);
+    a.ntasks = s.ntasks;
     a.vec2 = s.vec2;
-    e = launch_boxcopy(a, s.max_rows, st);
+    e = launch_boxcopy(a, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   return TFFT_OK;
@@ -1241,6 +1347,7 @@ int tfft_plan_bind(tfft_plan p, void* d_state, size_t bytes, void* stream) {
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize (bind)");
     p->d_state = static_cast<char*>(d_state);
+    p->device = current_device();
     return TFFT_OK;
   });
 }
@@ -1260,7 +1367,7 @@ int tfft_plan_workspace_bytes(tfft_plan p, int mode, int keep_input, size_t* byt
 int tfft_redistribute(tfft_plan p, int axis_v, int axis_w, const void* in, void* out, void* stream) {
   return guarded("tfft_redistribute", [&]() -> int {
     if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (int rcb = check_bound(p)) return rcb;
     const int sf = p->g - axis_v, stt = p->g - axis_w;
     if (sf < 0 || sf > p->g || stt < 0 || stt > p->g || std::abs(sf - stt) != 1)
       return fail(TFFT_EINVAL, "axis_v / axis_w are not the aligned axes of two adjacent stages");
@@ -1272,8 +1379,7 @@ int tfft_redistribute(tfft_plan p, int axis_v, int axis_w, const void* in, void*
     const char* a = static_cast<const char*>(in);
     const char* b = static_cast<const char*>(out);
     if (a < b + bytes && b < a + bytes) return fail(TFFT_EINVAL, "in and out overlap");
-    const ExchangeBoxes& X = p->xboxes[{sf, stt}];
-    Step s = box_step(p, X.direct, p->xbox_off[{sf, stt}][0]);
+    Step s = box_step(p->xbox_off[{sf, stt}][0]);
     s.src = BUF_IN;
     s.dst = BUF_OUT;
     void* bufs[4] = {const_cast<void*>(in), out, nullptr, nullptr};
@@ -1284,7 +1390,7 @@ int tfft_redistribute(tfft_plan p, int axis_v, int axis_w, const void* in, void*
 int tfft_partial(tfft_plan p, int stage, int axis, int sign, void* inout, void* stream) {
   return guarded("tfft_partial", [&]() -> int {
     if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (int rcb = check_bound(p)) return rcb;
     if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
     if (axis < 0 || axis >= p->d) return fail(TFFT_EINVAL, "axis out of range");
     if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
@@ -1336,16 +1442,7 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
     }
     if (s.kind == S_BOX) {
       nm = "box_copy";
-      const ExchangeBoxes* X = nullptr;
-      for (auto& kv : p->xbox_off)
-        for (int k = 0; k < 4; ++k)
-          if (kv.second[k] == s.box_off) {
-            const ExchangeBoxes& E = p->xboxes[kv.first];
-            const std::vector<BoxDesc>* v[4] = {&E.direct, &E.pack, &E.xchg, &E.unpack};
-            for (const BoxDesc& b : *v[k]) elems += b.ext[0] * b.ext[1] * b.ext[2] * b.ext[3];
-            X = &E;
-          }
-      (void)X;
+      elems = s.box_elems;
     } else {
       const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
       const bool tma = s.kind == S_STRIDED && s.tma;
@@ -1365,6 +1462,30 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
   });
 }
 
+int tfft_plan_copy_tasks(tfft_plan p, int sign, int mode, int index, int64_t* tasks, int64_t max_tasks,
+                         int64_t* ntasks) {
+  return guarded("tfft_plan_copy_tasks", [&]() -> int {
+    if (!p || !ntasks || (max_tasks > 0 && !tasks)) return fail(TFFT_EINVAL, "NULL argument");
+    auto it = p->steps.find({sign, mode});
+    if (it == p->steps.end()) return fail(TFFT_EINVAL, "bad sign or mode");
+    if (index < 0 || index >= (int)it->second.size()) return fail(TFFT_EINVAL, "launch index out of range");
+    const Step& s = it->second[index];
+    if (s.kind != S_BOX) return fail(TFFT_EINVAL, "launch is not a box copy");
+    *ntasks = s.ntasks;
+    const CopyTask* t = reinterpret_cast<const CopyTask*>(p->image.data() + s.box_off);
+    for (int64_t k = 0; k < std::min<int64_t>(max_tasks, s.ntasks); ++k) {
+      int64_t* o = tasks + 6 * k;
+      o[0] = t[k].src;
+      o[1] = t[k].dst;
+      o[2] = t[k].ss;
+      o[3] = t[k].ds;
+      o[4] = t[k].nrows;
+      o[5] = t[k].rowlen;
+    }
+    return TFFT_OK;
+  });
+}
+
 int tfft_plan_set_wait_limit(tfft_plan p, uint32_t polls) {
   if (!p) return fail(TFFT_EINVAL, "plan is NULL");
   p->wait_limit = polls > 0 ? polls : (1u << 22);
@@ -1373,7 +1494,7 @@ int tfft_plan_set_wait_limit(tfft_plan p, uint32_t polls) {
 
 int tfft_plan_device_status(tfft_plan p, int* status, int reset, void* stream) {
   if (!p || !status) return fail(TFFT_EINVAL, "NULL argument");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  if (int rcb = check_bound(p)) return rcb;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int v = 0;
   cudaError_t e = cudaMemcpyAsync(&v, p->d_state, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1400,7 +1521,7 @@ int tfft_plan_set_launch_events(tfft_plan p, void* const* events, int count) {
 }
 
 static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
-                        size_t work_bytes, void* stream, const double* coef = nullptr);
+                        size_t work_bytes, void* stream, const double* coef = nullptr, double factor = 1.0);
 
 int tfft_execute(tfft_plan p, int sign, int mode, const void* in, void* out, void* work,
                  size_t work_bytes, void* stream) {
@@ -1415,6 +1536,17 @@ int tfft_adjoint(tfft_plan p, int mode, const void* in, void* out, void* work, s
     if (p && p->kind != TFFT_C2C) return fail(TFFT_EUNSUPPORTED, "the adjoint is built for complex-to-complex plans");
     if (d_coef && (reinterpret_cast<uintptr_t>(d_coef) & 7)) return fail(TFFT_EINVAL, "d_coef is misaligned");
     return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, in, out, work, work_bytes, stream, d_coef);
+  });
+}
+
+int tfft_weighted_energy_grad(tfft_plan p, int mode, const void* u, void* out, void* work, size_t work_bytes,
+                              const double* d_g, void* stream) {
+  return guarded("tfft_weighted_energy_grad", [&]() -> int {
+    if (p && p->kind != TFFT_C2C) return fail(TFFT_EUNSUPPORTED, "the adjoint is built for complex-to-complex plans");
+    if (d_g && (reinterpret_cast<uintptr_t>(d_g) & 7)) return fail(TFFT_EINVAL, "d_g is misaligned");
+    // d/dRe x + i d/dIm x of g sum |F(x) w|^2 = 2 g F^H (w^2 F x): the factor 2
+    // joins the adjoint's own scale on its last pass, g is read there on the device
+    return execute_impl(p, kAdjoint, TFFT_BACKWARD, mode, u, out, work, work_bytes, stream, d_g, 2.0);
   });
 }
 
@@ -1470,7 +1602,7 @@ int tfft_execute_host(tfft_plan p, int nsigns, const int* signs, int count, cons
                       void* const* h_out, void* d_space, size_t space_bytes, void* stream) {
   return guarded("tfft_execute_host", [&]() -> int {
     if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (int rcb = check_bound(p)) return rcb;
     if (nsigns < 1 || !signs) return fail(TFFT_EINVAL, "need at least one transform direction");
     for (int j = 0; j < nsigns; ++j) {
       if (signs[j] != TFFT_FORWARD && signs[j] != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
@@ -1535,7 +1667,7 @@ int tfft_weighted_energy(tfft_plan p, int stage, const void* y, const float* w, 
                          void* stream) {
   return guarded("tfft_weighted_energy", [&]() -> int {
     if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (int rcb = check_bound(p)) return rcb;
     if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
     int rc = check_ptr(y, "y");
     if (rc) return rc;
@@ -1554,7 +1686,7 @@ int tfft_weight_scale(tfft_plan p, int stage, const void* y, const float* w, con
                       void* z, void* stream) {
   return guarded("tfft_weight_scale", [&]() -> int {
     if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-    if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+    if (int rcb = check_bound(p)) return rcb;
     if (stage < 0 || stage > p->g) return fail(TFFT_EINVAL, "stage out of range");
     int rc = check_ptr(y, "y");
     if (rc) return rc;
@@ -1569,9 +1701,9 @@ int tfft_weight_scale(tfft_plan p, int stage, const void* y, const float* w, con
 }
 
 static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
-                        size_t work_bytes, void* stream, const double* coef) {
+                        size_t work_bytes, void* stream, const double* coef, double factor) {
   if (!p) return fail(TFFT_EINVAL, "plan is NULL");
-  if (!p->d_state) return fail(TFFT_ESTATE, "plan is not bound");
+  if (int rcb = check_bound(p)) return rcb;
   if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
   if (mode < TFFT_MODE_FUSED || mode > TFFT_MODE_PACKED) return fail(TFFT_EINVAL, "unknown mode");
   if (!p->transformable) return fail(TFFT_EUNSUPPORTED, "an axis length has no transform plan (2/3/5 lengths up to 4096, others up to 2048)");
@@ -1590,12 +1722,14 @@ static int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in
     if (a < b + out_bytes && b < a + in_bytes) return fail(TFFT_EINVAL, "in and out overlap");
   }
   std::vector<Step> steps = p->steps[{key, mode}];
-  if (coef) {  // the device factor goes on the last transform pass
+  if (coef || factor != 1.0) {  // device coefficient and host factor go on the last transform pass
     int k = (int)steps.size() - 1;
     while (k >= 0 && steps[k].kind == S_BOX) --k;
     if (k < 0 || steps[k].kind != S_CONTIG)
       return fail(TFFT_EUNSUPPORTED, "a device coefficient needs a contiguous last pass");
     steps[k].coef = coef;
+    steps[k].scale_value = (steps[k].scaled ? steps[k].scale_value : 1.0) * factor;
+    steps[k].scaled = true;
   }
   void* w0 = nullptr;
   void* w1 = nullptr;

@@ -6,6 +6,7 @@
 #include <string>
 
 #include "tfft_common.cuh"
+#include "tfft_device_cache.h"
 
 namespace tfft {
 
@@ -13,6 +14,7 @@ namespace tfft {
 // tfft_plan_device_status()).
 constexpr int TFFT_DEVICE_ETIMEOUT = 1;  // a bounded wait on a copy expired
 constexpr int TFFT_DEVICE_EALIGN = 2;    // a TMA tile buffer was not 128-byte aligned (copy skipped)
+constexpr int TFFT_DEVICE_ETMEM = 4;     // MMAs still running after the clean-up wait: tensor memory not released
 
 // Batched 1-D FFT of contiguous lines (the axis held whole and innermost,
 // Eq. pencil0 / slab0): line l of the buffer is elements [l L, (l + 1) L).
@@ -187,17 +189,27 @@ struct BoxDesc {
   int64_t ds[MAXD];
 };
 
+// What the copy kernel runs: a box cut into 2-D tasks of nrows rows of
+// rowlen contiguous elements, rows ss / ds elements apart, from src / dst
+// (element offsets).  The planner merges box dimensions that are contiguous
+// on both sides first, so rows are as long as the layouts allow.
+struct CopyTask {
+  int64_t src, dst;
+  int64_t ss, ds;
+  int32_t nrows, rowlen;
+};
+
 struct BoxArgs {
   const float2* in;
   float2* out;
-  const BoxDesc* boxes;
-  int nboxes;
-  int vec2;  // every offset, stride and innermost extent is even: copy pairs
+  const CopyTask* tasks;
+  int64_t ntasks;
+  int vec2;  // every offset, stride and row length is even: 16-byte copies
 };
 
 cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s);
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
-cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s);
+cudaError_t launch_boxcopy(const BoxArgs& a, cudaStream_t s);
 cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStream_t s);
 cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
@@ -257,6 +269,20 @@ cudaError_t launch_weight_scale(const float2* y, const float* w, const double* c
 
 // Message returned by tfft_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
+
+// The current device id (-1 if the runtime cannot tell) and its SM count
+// (cached per device).
+int current_device();
+int device_sm_count();
+
+// The kernel's maximum dynamic shared memory set once per device (the
+// attribute is per device); `cache` is the caller's static for that kernel.
+template <class K>
+cudaError_t smem_attr_once(PerDevice<cudaError_t>& cache, K kernel, int bytes) {
+  return cache.get(current_device(), [&] {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  });
+}
 
 // Limits of the kernels, used by the planner.
 bool kernel_supports_E(int E);

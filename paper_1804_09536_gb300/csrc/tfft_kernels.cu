@@ -437,37 +437,37 @@ __global__ void __launch_bounds__(512) k_blue_strided(const StridedArgs a, const
 
 // ------------------------------------------------------------ box copy
 
+// One CTA per copy task.  The task's rows are spread over the CTA in slots of
+// `lpr` lanes (the smallest power of two covering the row, at most 256), and
+// every thread keeps U rows' loads in flight before it stores them; no
+// division per row or element.  T is float4 (pairs of complex64) when every
+// offset, stride and row length of the launch is even, else float2.
+template <class T, int U>
 __global__ void __launch_bounds__(256) k_boxcopy(const BoxArgs a) {
-  const BoxDesc* bp = a.boxes + blockIdx.y;
-  const int64_t e0 = bp->ext[0], e1 = bp->ext[1], e2 = bp->ext[2];
-  const int64_t rowlen = a.vec2 ? bp->ext[3] / 2 : bp->ext[3];  // in copy units
-  const int64_t nrows = e0 * e1 * e2;
-  if (nrows == 0 || rowlen == 0) return;
-  // lanes per row: the smallest power of two >= rowlen, at most 32
-  int lpr = 1;
-  while (lpr < 32 && lpr < rowlen) lpr <<= 1;
-  const int rpw = 32 / lpr;  // rows per warp
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  const int sub = lane / lpr, l = lane - sub * lpr;
-  const int64_t s0 = bp->ss[0], s1 = bp->ss[1], s2 = bp->ss[2];
-  const int64_t d0 = bp->ds[0], d1 = bp->ds[1], d2 = bp->ds[2];
-  const int64_t sb = bp->src, db = bp->dst;
-  for (int64_t row = ((int64_t)blockIdx.x * wpc + warp) * rpw + sub; row < nrows;
-       row += (int64_t)gridDim.x * wpc * rpw) {
-    const int64_t i2 = row % e2;
-    const int64_t t = row / e2;
-    const int64_t i1 = t % e1;
-    const int64_t i0 = t / e1;
-    const int64_t so = sb + i0 * s0 + i1 * s1 + i2 * s2;
-    const int64_t dof = db + i0 * d0 + i1 * d1 + i2 * d2;
-    if (a.vec2) {
-      const float4* src = reinterpret_cast<const float4*>(a.in + so);
-      float4* dst = reinterpret_cast<float4*>(a.out + dof);
-      for (int64_t c = l; c < rowlen; c += lpr) dst[c] = src[c];
-    } else {
-      const float2* src = a.in + so;
-      float2* dst = a.out + dof;
-      for (int64_t c = l; c < rowlen; c += lpr) dst[c] = src[c];
+  constexpr int K = sizeof(T) / sizeof(float2);
+  const CopyTask* tp = a.tasks + blockIdx.x;
+  const int nrows = tp->nrows;
+  const int rowlen = tp->rowlen / K;  // in copy units
+  if (nrows <= 0 || rowlen <= 0) return;
+  const T* src = reinterpret_cast<const T*>(a.in + tp->src);
+  T* dst = reinterpret_cast<T*>(a.out + tp->dst);
+  const int64_t ss = tp->ss / K, ds = tp->ds / K;
+  const int lpr = rowlen >= 256 ? 256 : (rowlen <= 1 ? 1 : 1 << (32 - __clz(rowlen - 1)));
+  const int slots = 256 / lpr;
+  const int lane = threadIdx.x % lpr, slot = threadIdx.x / lpr;
+  for (int r0 = slot; r0 < nrows; r0 += slots * U) {
+    for (int c = lane; c < rowlen; c += lpr) {
+      T v[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int r = r0 + k * slots;
+        if (r < nrows) v[k] = src[r * ss + c];
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int r = r0 + k * slots;
+        if (r < nrows) dst[r * ds + c] = v[k];
+      }
     }
   }
 }
@@ -486,16 +486,16 @@ __global__ void k_twiddles(float2* tw, int L) {
   }
 }
 
-template <class K>
-cudaError_t allow_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-}
+// the kernel's shared-memory limit raised to 227 KB, once per device
+#define TFFT_ALLOW_SMEM(kernel)                          \
+  static PerDevice<cudaError_t> attr_cache;              \
+  const cudaError_t attr = smem_attr_once(attr_cache, kernel, 227 * 1024)
 
 constexpr int64_t kMaxGrid = 1 << 20;
 
 template <int E>
 cudaError_t launch_contig_E(const ContigArgs& a, cudaStream_t s) {
-  static cudaError_t attr = allow_smem(k_fft_contig<E>);
+  TFFT_ALLOW_SMEM(k_fft_contig<E>);
   if (attr != cudaSuccess) return attr;
   const int B = a.lines_per_cta;
   const int L = a.ap.L;
@@ -509,7 +509,7 @@ cudaError_t launch_contig_E(const ContigArgs& a, cudaStream_t s) {
 
 template <int E>
 cudaError_t launch_strided_E(const StridedArgs& a, cudaStream_t s) {
-  static cudaError_t attr = allow_smem(k_fft_strided<E>);
+  TFFT_ALLOW_SMEM(k_fft_strided<E>);
   if (attr != cudaSuccess) return attr;
   const int L = a.ap.L;
   const size_t smem = (size_t)L * a.W * sizeof(float2) + 2 * (size_t)L * sizeof(int64_t);
@@ -539,7 +539,7 @@ bool kernel_supports_E(int E) {
 cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
   if (a.ap.spec) return launch_contig_spec(a, s);
   if (a.ap.E == 0) {
-    static cudaError_t attr = allow_smem(k_fft_contig_generic);
+    TFFT_ALLOW_SMEM(k_fft_contig_generic);
     if (attr != cudaSuccess) return attr;
     const int B = a.lines_per_cta;
     const size_t smem = 2 * (size_t)B * a.ap.L * sizeof(float2);
@@ -563,7 +563,7 @@ cudaError_t launch_contig(const ContigArgs& a, cudaStream_t s) {
 cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
   if (a.ap.spec) return launch_strided_spec(a, s);
   if (a.ap.E == 0) {
-    static cudaError_t attr = allow_smem(k_fft_strided_generic);
+    TFFT_ALLOW_SMEM(k_fft_strided_generic);
     if (attr != cudaSuccess) return attr;
     const int L = a.ap.L;
     const size_t smem = 2 * (size_t)L * a.W * sizeof(float2) + 2 * (size_t)L * sizeof(int64_t);
@@ -585,7 +585,7 @@ cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStream_t s) {
-  static cudaError_t attr = allow_smem(k_blue_contig);
+  TFFT_ALLOW_SMEM(k_blue_contig);
   if (attr != cudaSuccess) return attr;
   const int B = a.lines_per_cta;
   const size_t smem = 2 * (size_t)B * b.M * sizeof(float2);
@@ -597,7 +597,7 @@ cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStrea
 }
 
 cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStream_t s) {
-  static cudaError_t attr = allow_smem(k_blue_strided);
+  TFFT_ALLOW_SMEM(k_blue_strided);
   if (attr != cudaSuccess) return attr;
   const size_t smem = 2 * (size_t)b.M * a.W * sizeof(float2) + 2 * (size_t)b.N * sizeof(int64_t);
   int64_t grid = a.nouter * a.ncolblocks;
@@ -607,14 +607,30 @@ cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_boxcopy(const BoxArgs& a, int64_t max_rows, cudaStream_t s) {
-  if (a.nboxes <= 0) return cudaSuccess;
-  if (a.nboxes > 65535) return cudaErrorInvalidConfiguration;
-  int64_t gx = (max_rows + 7) / 8;  // 8 warps, at least one row each
-  if (gx < 1) gx = 1;
-  if (gx > 65535) gx = 65535;
-  k_boxcopy<<<dim3((unsigned)gx, (unsigned)a.nboxes), 256, 0, s>>>(a);
+cudaError_t launch_boxcopy(const BoxArgs& a, cudaStream_t s) {
+  if (a.ntasks <= 0) return cudaSuccess;
+  if (a.ntasks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  if (a.vec2)
+    k_boxcopy<float4, 4><<<(unsigned)a.ntasks, 256, 0, s>>>(a);
+  else
+    k_boxcopy<float2, 4><<<(unsigned)a.ntasks, 256, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+  return dev;
+}
+
+int device_sm_count() {
+  static PerDevice<int> cache;
+  const int dev = current_device();
+  return cache.get(dev, [dev] {
+    int v = 0;
+    if (dev < 0 || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) v = 0;
+    return v > 0 ? v : 1;
+  });
 }
 
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s) {

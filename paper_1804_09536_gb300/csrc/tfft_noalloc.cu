@@ -7,11 +7,12 @@
 // device memory through its own allocator and forbids (or has no memory left
 // for) a stray cudaMalloc, or code with a fixed, audited memory budget.  Such
 // a caller can still keep its input intact, which tfft_execute() only does
-// when it is given a workspace.
+// when it is given a workspace.  The one exception is the complex-to-real
+// backward of a real-to-complex plan: it overwrites its input with either
+// entry point.
 //
 // The scratch is one stage buffer: the fused path writes the input's
 // partially transformed copy there before it redistributes it into `out`.
-#include <mutex>
 #include <string>
 
 #include "tfft.h"
@@ -26,32 +27,26 @@ constexpr size_t kNoallocScratchBytes = TFFT_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-// Device address of the array per device.  In host code the array's name is
-// only a host-side stand-in, so the address is looked up with
-// cudaGetSymbolAddress, once per device, with that device current.
-constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mutex;
-
+// Device address of the array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress, with the device current, on every call: the lookup is
+// cheap once the module is loaded, and a cached address would go stale after
+// a device reset.
 int scratch_for_current_device(void** ptr) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TFFT_ECUDA;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return TFFT_ECUDA;
-    g_scratch_ptr[dev] = p;
-  }
-  *ptr = g_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return TFFT_ECUDA;
+  *ptr = p;
   return TFFT_OK;
 }
 
 }  // namespace
 
 extern "C" int tfft_execute_noalloc(tfft_plan plan, int sign, const void* in, void* out, void* stream) {
-  if (!plan) return TFFT_EINVAL;
+  if (!plan) {
+    tfft::set_last_error("tfft_execute_noalloc: plan is NULL");
+    return TFFT_EINVAL;
+  }
   size_t need = 0;
   int rc = tfft_plan_workspace_bytes(plan, TFFT_MODE_FUSED, 1, &need);
   if (rc != TFFT_OK) return rc;
@@ -67,5 +62,7 @@ extern "C" int tfft_execute_noalloc(tfft_plan plan, int sign, const void* in, vo
     tfft::set_last_error("tfft_execute_noalloc: cudaGetSymbolAddress of the scratch array failed");
     return rc;
   }
+  // tfft_execute() rejects (TFFT_EINVAL) a current device other than the one
+  // the plan was bound on, so the scratch is always the plan's device's array
   return tfft_execute(plan, sign, TFFT_MODE_FUSED, in, out, scratch, kNoallocScratchBytes, stream);
 }

@@ -43,16 +43,16 @@ __global__ void __launch_bounds__(W * (L / E), min_blocks(E, W * (L / E), 1024))
     strided_tile<L, E, W, false, Rs...>(a, tile, smem, threadIdx.x, opaque_tid_y(), tid, rp);
 }
 
-template <class K>
-cudaError_t allow_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-}
+// the kernel's shared-memory limit raised to 227 KB, once per device
+#define TFFT_ALLOW_SMEM(kernel)                          \
+  static PerDevice<cudaError_t> attr_cache;              \
+  const cudaError_t attr = smem_attr_once(attr_cache, kernel, 227 * 1024)
 
 constexpr int64_t kMaxGrid = 1 << 20;
 
 template <int L, int E, int B, int... Rs>
 cudaError_t run_contig(const ContigArgs& a, cudaStream_t s) {
-  static cudaError_t attr = allow_smem(k_contig_spec<L, E, B, Rs...>);
+  TFFT_ALLOW_SMEM((k_contig_spec<L, E, B, Rs...>));
   if (attr != cudaSuccess) return attr;
   const size_t smem = (size_t)B * line_pitch<L, Rs...>() * sizeof(float2);
   int64_t grid = (a.nlines + B - 1) / B;
@@ -64,19 +64,18 @@ cudaError_t run_contig(const ContigArgs& a, cudaStream_t s) {
 
 template <int L, int E, int W, int... Rs>
 cudaError_t run_strided(const StridedArgs& a, cudaStream_t s) {
-  static cudaError_t attr = allow_smem(k_strided_spec<L, E, W, Rs...>);
+  TFFT_ALLOW_SMEM((k_strided_spec<L, E, W, Rs...>));
   if (attr != cudaSuccess) return attr;
   if (a.W != W) return cudaErrorInvalidValue;
   constexpr size_t smem = strided_tile_smem<L, W>(strided_cache_rows(L));
   // persistent: as many CTAs as fit at once, each taking every gridDim-th
   // tile, so that the row part table is computed once per CTA
-  static const int64_t slots = [] {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  static PerDevice<int64_t> slots_cache;
+  const int64_t slots = slots_cache.get(current_device(), [] {
+    int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strided_spec<L, E, W, Rs...>, W * (L / E), smem);
-    return (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  }();
+    return (int64_t)device_sm_count() * (per_sm > 0 ? per_sm : 1);
+  });
   int64_t grid = a.nouter * a.ncolblocks;
   if (grid > slots) grid = slots;
   if (grid < 1) return cudaSuccess;

@@ -169,10 +169,10 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
   }
 }
 
-template <class K>
-cudaError_t allow_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-}
+// the kernel's shared-memory limit raised to 227 KB, once per device
+#define TFFT_ALLOW_SMEM(kernel)                          \
+  static PerDevice<cudaError_t> attr_cache;              \
+  const cudaError_t attr = smem_attr_once(attr_cache, kernel, 227 * 1024)
 
 constexpr int64_t kMaxGrid = 1 << 20;
 
@@ -182,12 +182,12 @@ cudaError_t run_real(const RealArgs& a, cudaStream_t s) {
   const int64_t grid = grid0 > kMaxGrid ? kMaxGrid : grid0;
   if (grid < 1) return cudaSuccess;
   if (a.dir < 0) {
-    static cudaError_t attr = allow_smem(k_r2c_spec<L, E, B, Rs...>);
+    TFFT_ALLOW_SMEM((k_r2c_spec<L, E, B, Rs...>));
     if (attr != cudaSuccess) return attr;
     const size_t smem = (size_t)B * line_pitch<L, Rs...>() * sizeof(float2);
     k_r2c_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);
   } else {
-    static cudaError_t attr = allow_smem(k_c2r_spec<L, E, B, Rs...>);
+    TFFT_ALLOW_SMEM((k_c2r_spec<L, E, B, Rs...>));
     if (attr != cudaSuccess) return attr;
     const size_t smem = (size_t)B * (line_pitch<L, Rs...>() + 1) * sizeof(float2);
     k_c2r_spec<L, E, B, Rs...><<<(unsigned)grid, dim3(L / E, B), smem, s>>>(a);

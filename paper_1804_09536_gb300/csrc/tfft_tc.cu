@@ -184,6 +184,29 @@ __device__ __forceinline__ int tw_slot(int i) { return i + (i >> 4); }
 constexpr int kCtasPerSm = 4;                      // 4 x 64 of the 512 tensor-memory columns
 static_assert(kCtasPerSm * kTmemCols <= 512, "tensor memory columns per SM");
 
+// Range scaling of the FP16 operands.  A line's sub-transform inputs are
+// multiplied by 2^s, s chosen from their largest magnitude m so that m 2^s
+// lies in [2^14, 2^15): the hi parts then stay below the FP16 maximum (65504)
+// and the lo parts of everything within 2^17 of the maximum stay normal
+// (FP16 subnormals would cut their precision).  The power of two is exact in
+// FP32, and the accumulator is multiplied by 2^-s in the epilogue.  BF16 has
+// FP32's exponent range and needs no scaling.  s is clamped so that 2^s and
+// 2^-s are normal floats; a zero (or NaN) line keeps s = 0.
+__device__ __forceinline__ int fp16_range_shift(float m) {
+  if (!(m > 0.f)) return 0;
+  const int e = ((__float_as_int(m) >> 23) & 255) - 126;  // m < 2^e
+  const int sh = 15 - e;
+  return sh < -126 ? -126 : (sh > 126 ? 126 : sh);
+}
+__device__ __forceinline__ float exp2_int(int sh) { return __int_as_float((sh + 127) << 23); }
+
+// Second, clean-up wait for MMAs still in flight after a wait gave up: about
+// one second of clock cycles.  Tensor memory is released only once they are
+// known to be complete; if even this wait expires, the CTA leaves it
+// allocated (status TFFT_DEVICE_ETMEM) rather than free memory an MMA may
+// still write.
+constexpr long long kCleanupCycles = 2000000000LL;
+
 template <int FMT>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const ContigArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
@@ -194,6 +217,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
   float2* s_tw = reinterpret_cast<float2*>(b_lo + kBBytes);  // the twiddles jt * r1 < 512, padded
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_tw + kTwSlots);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  float* s_unscale = reinterpret_cast<float*>(tmem_slot + 1);  // 2^-s per line (FP16)
   const int tid = threadIdx.x, warp = tid >> 5;
   const int jt = tid % kT, ly = tid / kT;
   const bool inv = a.sign > 0;
@@ -231,26 +255,44 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
   bool failed = false;
   uint32_t phase = 0;
 
-  for (int64_t tile = blockIdx.x; tile * kLines < a.nlines; tile += gridDim.x) {
-    const int64_t line = tile * kLines + ly;
+  // the loads of a tile: thread jt of line ly holds x[jt + 16 r], r < 32
+  float2 v[kE];
+  auto load_tile = [&](int64_t t) {
+    const int64_t line = t * kLines + ly;
     const bool act = line < a.nlines;
     const float2* src = a.in + line * kL;
-    // radix-32 stage: thread jt holds x[jt + 16 r], r < 32
-    float2 v[kE];
 #pragma unroll
-    for (int r = 0; r < kE; ++r) {
-      float2 x = act ? src[jt + kT * r] : make_float2(0.f, 0.f);
-      if (inv) x.y = -x.y;
-      v[r] = x;
-    }
+    for (int r = 0; r < kE; ++r) v[r] = act ? src[jt + kT * r] : make_float2(0.f, 0.f);
+  };
+  if ((int64_t)blockIdx.x * kLines < a.nlines) load_tile(blockIdx.x);
+
+  for (int64_t tile = blockIdx.x; tile * kLines < a.nlines; tile += gridDim.x) {
+    // radix-32 stage on the loaded values
+#pragma unroll
+    for (int r = 0; r < kE; ++r)
+      if (inv) v[r].y = -v[r].y;
     Dft<32>::run(v);
     // output r1 of this thread is input jt of sub-transform j = r1; twiddle
-    // exp(-2 pi i jt r1 / 512), then the A rows (line, r1), columns 2 jt, 2 jt + 1
+    // exp(-2 pi i jt r1 / 512)
+#pragma unroll
+    for (int r1 = 1; r1 < kE; ++r1)
+      if (jt != 0) v[r1] = cmul(v[r1], s_tw[tw_slot(jt * r1)]);
+    float sc = 1.f;
+    if constexpr (FMT == 0) {
+      float m = 0.f;
+#pragma unroll
+      for (int r1 = 0; r1 < kE; ++r1) m = fmaxf(m, fmaxf(fabsf(v[r1].x), fabsf(v[r1].y)));
+#pragma unroll
+      for (int o = 8; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));  // the line's 16 lanes
+      const int sh = fp16_range_shift(m);
+      sc = exp2_int(sh);
+      if (jt == 0) s_unscale[ly] = exp2_int(-sh);
+    }
+    // the A rows (line, r1), columns 2 jt, 2 jt + 1
 #pragma unroll
     for (int r1 = 0; r1 < kE; ++r1) {
-      const float2 t = (jt * r1 == 0) ? v[r1] : cmul(v[r1], s_tw[tw_slot(jt * r1)]);
       uint32_t lo;
-      const uint32_t hi = Half16<FMT>::pack_hi_lo(t.x, t.y, lo);
+      const uint32_t hi = Half16<FMT>::pack_hi_lo(v[r1].x * sc, v[r1].y * sc, lo);
       const uint32_t off = op_off(ly * 32 + r1, 2 * jt);
       *reinterpret_cast<uint32_t*>(a_hi + off) = hi;
       *reinterpret_cast<uint32_t*>(a_lo + off) = lo;
@@ -275,6 +317,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
       }
       umma_commit(bar);
     }
+    // the next tile's loads, in flight while the MMAs and this tile's epilogue run
+    {
+      const int64_t next = tile + gridDim.x;
+      if (next * kLines < a.nlines) load_tile(next);
+    }
     // bounded wait for the MMAs (first poll non-blocking)
     bool ok = mbar_test(bar, phase);
     for (uint32_t i = 1; i < a.wait_limit && !ok; ++i) ok = mbar_try(bar, phase);
@@ -296,9 +343,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
       if (gl < a.nlines) {
         float2* dst = a.out + gl * kL;
         const int j = tid & 31;
+        const float f = (FMT == 0) ? oscale * s_unscale[lline] : oscale;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          float2 y = make_float2(r[2 * k] * oscale, r[2 * k + 1] * oscale);
+          float2 y = make_float2(r[2 * k] * f, r[2 * k + 1] * f);
           if (inv) y.y = -y.y;
           dst[j + 32 * k] = y;
         }
@@ -308,32 +356,31 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_contig_tc512(const Con
     __syncthreads();  // TMEM and the A operands are free for the next tile
     tc_fence_after();
   }
+  // after a wait gave up, the MMAs of that tile may still be running: wait
+  // for their commit (bounded by time, not by the requested poll limit,
+  // which may have been tiny on purpose) before their memory is released
+  int drained = 1;
   if (failed && tid == 0) {
-    // let the outstanding MMAs finish before their tensor memory is released
-    // (a fixed, generous bound: the requested limit may have been tiny)
-    for (uint32_t i = 0; i < (1u << 22); ++i)
-      if (mbar_try(bar, phase ^ 1)) break;
+    drained = 0;
+    const long long t0 = clock64();
+    while (!drained && clock64() - t0 < kCleanupCycles) drained = mbar_try(bar, phase ^ 1) ? 1 : 0;
+    if (!drained) atomicOr(a.status, TFFT_DEVICE_ETMEM);
   }
   tc_fence_before();
-  __syncthreads();
+  drained = __syncthreads_and(drained);
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0 && drained) tmem_dealloc(tmem, kTmemCols);
 }
 
 template <int FMT>
 cudaError_t run_tc(const ContigArgs& a, cudaStream_t s) {
-  const size_t smem = 2 * kOpBytes + 2 * kBBytes + kTwSlots * sizeof(float2) + 16;
-  static cudaError_t attr =
-      cudaFuncSetAttribute(k_contig_tc512<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = 2 * kOpBytes + 2 * kBBytes + kTwSlots * sizeof(float2) + 16 + kLines * sizeof(float);
+  static PerDevice<cudaError_t> attr_cache;
+  const cudaError_t attr = smem_attr_once(attr_cache, k_contig_tc512<FMT>, (int)smem);
   if (attr != cudaSuccess) return attr;
   // kCtasPerSm resident CTAs per SM (the launch bounds' promise); the grid
   // is a persistent tile loop, so extra CTAs would only queue
-  static const int slots = [] {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (sms > 0 ? sms : 1) * kCtasPerSm;
-  }();
+  const int slots = device_sm_count() * kCtasPerSm;
   const int64_t ntiles = (a.nlines + kLines - 1) / kLines;
   const int64_t grid = ntiles < slots ? ntiles : slots;
   if (grid < 1) return cudaSuccess;

@@ -152,27 +152,17 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
   if (tid == 0) bulk_wait_all();
 }
 
-template <class K>
-cudaError_t allow_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-}
-
-int sm_count() {
-  static int n = [] {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    return v > 0 ? v : 1;
-  }();
-  return n;
-}
+// the kernel's shared-memory limit raised to 227 KB, once per device
+#define TFFT_ALLOW_SMEM(kernel)                          \
+  static PerDevice<cudaError_t> attr_cache;              \
+  const cudaError_t attr = smem_attr_once(attr_cache, kernel, 227 * 1024)
 
 template <class K>
 int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (per_sm < 1) per_sm = 1;
-  const int64_t g = (int64_t)per_sm * sm_count();
+  const int64_t g = (int64_t)per_sm * device_sm_count();
   return ntiles < g ? ntiles : g;
 }
 
@@ -180,12 +170,14 @@ template <int L, int E, int W, int... Rs>
 cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo& go, const CUtensorMap& ti,
                             const CUtensorMap& to, cudaStream_t s) {
   auto kern = k_strided_tma<L, E, W, Rs...>;
-  static cudaError_t attr = allow_smem(kern);
+  TFFT_ALLOW_SMEM(kern);
   if (attr != cudaSuccess) return attr;
   if (a.W != W) return cudaErrorInvalidValue;
   const size_t smem = strided_tma_smem(L, W);
   const int threads = W * (L / E);
-  static const int64_t slots = persistent_grid(kern, threads, smem, int64_t(1) << 40);
+  static PerDevice<int64_t> slots_cache;
+  const int64_t slots =
+      slots_cache.get(current_device(), [&] { return persistent_grid(kern, threads, smem, int64_t(1) << 40); });
   const int64_t ntiles = a.nouter * a.ncolblocks;
   const int64_t grid = ntiles < slots ? ntiles : slots;
   if (grid < 1) return cudaSuccess;

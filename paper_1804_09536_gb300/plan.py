@@ -210,6 +210,21 @@ class Plan:
         call("tfft_weighted_energy", self._h, stage, _ptr(y), _ptr(w), _ptr(out), up, _stream_ptr(stream))
         return out
 
+    def weighted_energy_grad(self, u: torch.Tensor, g: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                             mode: str = "fused", keep_input: bool = True, stream=None) -> torch.Tensor:
+        """2 g F^H u (stage g -> stage 0): the gradient of g * sum |F(x) w|^2 given
+        u = w^2 F(x) from ``weighted_energy(..., u=...)``; ``g`` is a float64 0-d
+        device tensor read on the device (None: g = 1)."""
+        if out is None:
+            out = self.empty_stage(0)
+        work = self.workspace(mode, keep_input)
+        wp = _ptr(work) if work is not None else ctypes.c_void_p(0)
+        wb = work.numel() * work.element_size() if work is not None else 0
+        gp = _ptr(g) if g is not None else ctypes.c_void_p(0)
+        call("tfft_weighted_energy_grad", self._h, _MODES[mode], _ptr(u), _ptr(out), wp, wb, gp,
+             _stream_ptr(stream))
+        return out
+
     def weight_scale(self, stage: int, y: torch.Tensor, w: torch.Tensor, coef: torch.Tensor | None,
                      scale: float, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """z = scale * coef * w^2 * y elementwise (coef: float64 0-d device tensor or None)."""

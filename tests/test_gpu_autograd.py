@@ -119,6 +119,21 @@ def test_adjoint_device_coefficient(cuda_device, mode):
     assert rel_l2(b.cpu().numpy(), -2.75 * a.cpu().numpy()) <= 1e-6
 
 
+@pytest.mark.parametrize("mode", ["fused", "unfused", "packed"])
+@pytest.mark.parametrize("norm", ["forward", "backward"])
+def test_weighted_energy_grad_is_twice_g_times_the_adjoint(cuda_device, mode, norm):
+    """tfft_weighted_energy_grad(u, g) = 2 g F^H u with g read on the device (and g = 1
+    when none is given), under both normalisations."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (32, 32, 32), (2, 2)
+    p = Plan(shape, grid, norm=norm, device=cuda_device)
+    u = to_dev(R.scatter(inputs.normal_complex(shape, seed=12).numpy(), grid, 2), cuda_device)
+    g = torch.tensor(0.375, dtype=torch.float64, device=cuda_device)
+    a = p.adjoint(u, mode=mode).cpu().numpy()
+    assert rel_l2(p.weighted_energy_grad(u, g, mode=mode).cpu().numpy(), 0.75 * a) <= 1e-6
+    assert rel_l2(p.weighted_energy_grad(u, None, mode=mode).cpu().numpy(), 2.0 * a) <= 1e-6
+
+
 @pytest.mark.slow
 def test_full_size_512_loss_and_gradient_properties(cuda_device):
     """The differentiable workload of bench.py (512^3, 4 x 8), through the properties that

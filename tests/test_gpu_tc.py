@@ -40,6 +40,41 @@ def test_tc_forward_inverse_vs_oracle(cuda_device, precision, shape, grid):
     assert rel_l2(yf.cpu().numpy(), want) <= RTOL_FP32
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("scale", [1e-6, 1e4])
+def test_tc_range_of_the_operands(cuda_device, precision, scale):
+    """Inputs far from O(1): x 1e4 drives the radix-16 operands past FP16's maximum
+    (65504) and x 1e-6 into its subnormals unless each line is range-scaled; the
+    error relative to the oracle stays within the same bar."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (8, 16, 512), (2, 2)
+    x = (inputs.normal_complex(shape, seed=1) * scale).numpy()
+    b0 = R.scatter(x, grid, 0)
+    p = Plan(shape, grid, device=cuda_device, precision=precision)
+    y = p.forward(to_dev(b0, cuda_device))
+    torch.cuda.synchronize()
+    want = dft.distributed_forward(b0.astype(np.complex128), shape, grid)
+    assert np.all(np.isfinite(y.cpu().numpy()))
+    assert rel_l2(y.cpu().numpy(), want) <= BARS[precision]
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
+def test_tc_inverse_of_an_o1_spectrum(cuda_device, precision):
+    """The backward transform is unscaled (Eq. 2): an O(1) spectrum concentrated at
+    k = 0 (ones plus 1 % noise) grows to 64 x 64 x 32 = 131072 on the radix-16
+    operands of the last, contiguous pass -- twice the FP16 maximum."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (64, 64, 512), (2, 2)
+    yhat = (1.0 + 0.01 * inputs.normal_complex(shape, seed=2)).numpy().astype(np.complex64)
+    b2 = R.scatter(yhat, grid, 2)
+    p = Plan(shape, grid, device=cuda_device, precision=precision)
+    z = p.inverse(to_dev(b2, cuda_device))
+    torch.cuda.synchronize()
+    want = dft.distributed_backward(b2.astype(np.complex128), shape, grid)
+    assert np.all(np.isfinite(z.cpu().numpy()))
+    assert rel_l2(z.cpu().numpy(), want) <= 2 * BARS[precision]
+
+
 def test_tc_partial_tiles(cuda_device):
     """Lines that do not fill the last 8-line tile."""
     from paper_1804_09536_gb300.plan import Plan
