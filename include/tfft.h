@@ -65,9 +65,11 @@ typedef struct tfft_plan_s *tfft_plan;
 
 enum { TFFT_FORWARD = -1, TFFT_BACKWARD = +1 };
 enum { TFFT_C2C = 0, TFFT_R2C = 1 };
-/* precision: FP32 butterflies everywhere, or the radix-16 stage of length-512
-   contiguous passes on the tensor cores with split hi/lo BF16 or FP16 operands
-   and FP32 accumulation (other passes stay FP32) */
+/* precision: FP32 butterflies everywhere, or the last radix-16 stage on the
+   tensor cores with split hi/lo BF16 or FP16 operands (FP16 range-scaled per
+   line by a power of two) and FP32 accumulation, in length-512 contiguous
+   passes and in the TMA-staged strided passes of lengths 512 and 256 (other
+   passes stay FP32) */
 enum { TFFT_FP32 = 0, TFFT_TC_BF16X3 = 1, TFFT_TC_FP16X3 = 2 };
 /* plan flags */
 enum {

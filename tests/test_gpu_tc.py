@@ -17,14 +17,28 @@ pytestmark = pytest.mark.gpu
 BARS = {"bf16x3": 2e-5, "fp16x3": 1e-6}   # measured on 8 x 16 x 512: 3.1e-6, 2.7e-7
 
 
+TC_CASES = [
+    ((8, 16, 512), (2, 2)),         # contiguous 512 pass on the tensor cores
+    ((32, 24, 512), (4, 8)),
+    ((4, 4, 512), ()),
+    ((512, 64, 64), (4, 2)),        # strided TMA 512 pass on the tensor cores (axis 0)
+    ((256, 128, 256), (2, 4)),      # strided TMA 256 pass (axis 0) and contiguous 256 (FP32)
+    ((64, 512, 512), (2, 4)),       # strided 512 on axis 1 and contiguous 512, both on the tensor cores
+    ((96, 256, 128), (2, 2)),       # strided 256 on axis 1 between FP32 passes
+]
+
+
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
-@pytest.mark.parametrize("shape,grid", [((8, 16, 512), (2, 2)), ((32, 24, 512), (4, 8)), ((4, 4, 512), ())])
+@pytest.mark.parametrize("shape,grid", TC_CASES)
 def test_tc_forward_inverse_vs_oracle(cuda_device, precision, shape, grid):
     from paper_1804_09536_gb300.plan import Plan
     g = len(grid)
     x = inputs.normal_complex(shape, seed=0).numpy()
     p = Plan(shape, grid, device=cuda_device, precision=precision)
-    assert any("_tc_" in n for n, _ in p.launch_info(-1))
+    names = [n for n, _ in p.launch_info(-1)]
+    assert any("_tc_" in n for n in names), names
+    if 512 in shape[:-1] or 256 in shape[:-1]:
+        assert any(n.startswith("fft_strided_tma_tc_") for n in names), names
     b0 = R.scatter(x, grid, 0)
     y = p.forward(to_dev(b0, cuda_device))
     torch.cuda.synchronize()
@@ -42,12 +56,13 @@ def test_tc_forward_inverse_vs_oracle(cuda_device, precision, shape, grid):
 
 @pytest.mark.parametrize("precision", ["bf16x3", "fp16x3"])
 @pytest.mark.parametrize("scale", [1e-6, 1e4])
-def test_tc_range_of_the_operands(cuda_device, precision, scale):
+@pytest.mark.parametrize("shape,grid", [((8, 16, 512), (2, 2)), ((512, 32, 32), (2, 2))])
+def test_tc_range_of_the_operands(cuda_device, precision, scale, shape, grid):
     """Inputs far from O(1): x 1e4 drives the radix-16 operands past FP16's maximum
     (65504) and x 1e-6 into its subnormals unless each line is range-scaled; the
-    error relative to the oracle stays within the same bar."""
+    error relative to the oracle stays within the same bar (contiguous and strided
+    tensor-core passes)."""
     from paper_1804_09536_gb300.plan import Plan
-    shape, grid = (8, 16, 512), (2, 2)
     x = (inputs.normal_complex(shape, seed=1) * scale).numpy()
     b0 = R.scatter(x, grid, 0)
     p = Plan(shape, grid, device=cuda_device, precision=precision)
@@ -101,6 +116,29 @@ def test_tc_wait_expiry_reports_status(cuda_device):
     torch.cuda.synchronize()
     assert p.device_status() == 0
     want = dft.fftn_forward(x.cpu().numpy().reshape(shape).astype(np.complex128)).reshape(-1)
+    assert rel_l2(y.cpu().numpy(), want) <= BARS["bf16x3"]
+
+
+def test_tc_strided_wait_expiry_reports_status(cuda_device):
+    """The strided tensor-core pass with a one-poll limit on its copy and MMA waits:
+    the status word is set, tensor memory is released, the context stays usable and
+    a normal run afterwards is correct."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (512, 32, 32), (2, 2)
+    x = inputs.normal_complex(shape, seed=6).numpy()
+    b0 = R.scatter(x, grid, 0)
+    p = Plan(shape, grid, device=cuda_device, precision="bf16x3")
+    assert any(n.startswith("fft_strided_tma_tc_") for n, _ in p.launch_info(-1))
+    xd = to_dev(b0, cuda_device)
+    p.set_wait_limit(1)
+    p.forward(xd)
+    torch.cuda.synchronize()
+    assert p.device_status(reset=True) & 1
+    p.set_wait_limit(0)
+    y = p.forward(xd)
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    want = dft.distributed_forward(b0.astype(np.complex128), shape, grid)
     assert rel_l2(y.cpu().numpy(), want) <= BARS["bf16x3"]
 
 
