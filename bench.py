@@ -280,6 +280,11 @@ def run_ours(args):
                      tma=not args.no_tma, shape=(512, 512, 512), grid=(4, 8))
 
     # the 4-D case: 128^4 on a 3-D virtual grid
+    # the appendix's shape with non-2/3/5 lengths (127 by Bluestein) on a 3 x 4 grid
+    appa = appendix_a(plan_cls=Plan, dev=dev, steps=max(3, min(args.steps, 20)), barrier=barrier)
+    # the same kind of axis (127, Bluestein) in an array larger than L2
+    blue = appendix_a(plan_cls=Plan, dev=dev, steps=max(3, min(args.steps, 20)), barrier=barrier,
+                      shape=(512, 127, 512), grid=(4, 4))
     fd = fourd_128(plan_cls=Plan, dev=dev, steps=max(3, min(args.steps, 20)), barrier=barrier,
                    tma=not args.no_tma)
 
@@ -367,6 +372,8 @@ def run_ours(args):
         "r2c_slab_256": r2c,
         "r2c_pencil_512": r2c_p,
         "fourd_128": fd,
+        "appendix_a_42x127x256": appa,
+        "bluestein_512x127x512": blue,
         "tensor_core_512": tc,
         "autograd_512": ag,
         "batch48": bt,
@@ -626,6 +633,50 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), gri
             "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
             "note": "c2r overwrites its input; the forward output is reused as the inverse's input"}
+
+
+def appendix_a(plan_cls, dev, steps, barrier, shape=(42, 127, 256), grid=(3, 4)):
+    """App. A's 42 x 127 x 256 c2c on a 3 x 4 grid (42 = 2.3.7 and the prime 127 by
+    Bluestein's convolution form), or another shape: fused forward + inverse,
+    per-launch times and GB/s of algorithmic bytes (16 B per element per pass)."""
+    import torch
+    from paper_1804_09536_gb300 import inputs
+    p = plan_cls(shape, grid, device=dev)
+    x = p.scatter(inputs.uniform_complex(shape, seed=0).to(dev), 0)
+    y = p.empty_stage(p.g)
+    z = p.empty_stage(0)
+    w = p.workspace("fused", True)
+    stream = torch.cuda.current_stream()
+
+    def step(mode="fused", work=w, events=None):
+        if events is not None:
+            p.set_launch_events(events[0])
+        p.execute(-1, x, y, mode, work)
+        if events is not None:
+            p.set_launch_events(events[1])
+        p.execute(+1, y, z, mode, work)
+    for _ in range(3):
+        step()
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    barrier()
+    ms = a.elapsed_time(b) / steps
+    kernels = per_launch_times(p, step, "fused", w, steps, barrier, stream)
+    err = float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x))
+    n = math.prod(shape)
+    peak, _ = _peaks()
+    nbytes = sum(nb for _, nb in p.launch_info(-1) + p.launch_info(+1))
+    mib = 8 * n / 2**20
+    return {"workload": f"{'x'.join(map(str, shape))} c2c complex64 (lengths without a 2/3/5 factorisation by "
+                        f"Bluestein), virtual grid {'x'.join(map(str, grid))}, forward+inverse, fused; "
+                        f"{mib:.1f} MiB per stage buffer ({'L2-resident' if 8 * n < 129e6 else 'larger than L2'})",
+            "ms_per_step": round(ms, 4), "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+            "kernels": kernels, "round_trip_rel_l2": err}
 
 
 def fourd_128(plan_cls, dev, steps, barrier, tma=True):

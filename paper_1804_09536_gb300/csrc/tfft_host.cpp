@@ -967,7 +967,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
         at.colblocks = reinterpret_cast<const int2*>(p->d_state + s.tma_cb_off);
         at.ncolblocks = s.tma_ncb;
         at.outer_fastest = s.tma_outer_fastest ? 1 : 0;
-        if (p->precision != TFFT_FP32 && tc_strided_supported(s.L, s.tma_E, s.tma_W))
+        if (p->precision != TFFT_FP32 && tc_strided_supported(s.L, s.tma_E, s.tma_W, p->nelems))
           e = launch_strided_tma_tc(at, s.tma_E, p->precision, s.gin, s.gout, &ti, &to, st);
         else
           e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
@@ -1451,11 +1451,12 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
       const bool tma = s.kind == S_STRIDED && s.tma;
       const bool tc = p->precision != TFFT_FP32 &&
                       ((s.kind == S_CONTIG && tc_supported(ap.L)) ||
-                       (tma && tc_strided_supported(s.L, s.tma_E, s.tma_W)));
+                       (tma && tc_strided_supported(s.L, s.tma_E, s.tma_W, p->nelems)));
       nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
            (tma ? "_tma" : "") + (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : "") +
-           (ap.spec ? "_L" + std::to_string(ap.L) : ap.E == 0 ? std::string("_generic")
-                                                              : "_E" + std::to_string(ap.E));
+           (ap.blue_m ? "_bluestein_L" + std::to_string(ap.L)
+                      : ap.spec ? "_L" + std::to_string(ap.L)
+                                : ap.E == 0 ? std::string("_generic") : "_E" + std::to_string(ap.E));
       elems = p->nelems;
     }
     *bytes = 2 * elems * (int64_t)sizeof(float2);  // one read and one write of every element

@@ -108,6 +108,11 @@ struct StridedTilePos {
     go0 = (a.oax1 >= 0) ? o / a.on1 : o;
     go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
   }
+  // from an outer index and a column block already placed (any tile order)
+  __device__ __forceinline__ StridedTilePos(const StridedArgs& a, int64_t o, int2 b) : blk(b) {
+    go0 = (a.oax1 >= 0) ? o / a.on1 : o;
+    go1 = (a.oax1 >= 0) ? o - go0 * a.on1 : 0;
+  }
 };
 
 // The rows of one strided tile in one layout, with everything that does not
@@ -261,7 +266,7 @@ cudaError_t launch_contig_tc(const ContigArgs& a, int precision, cudaStream_t s)
 
 // Tensor-core strided TMA passes (tfft_tc_strided.cu): lengths 512 (E = 32,
 // W = 16) and 256 (E = 16, W = 32), the last radix-16 stage on tcgen05.
-bool tc_strided_supported(int L, int E, int W);
+bool tc_strided_supported(int L, int E, int W, int64_t nelems);
 cudaError_t launch_strided_tma_tc(const StridedArgs& a, int E, int precision, const TmaGeo& gin, const TmaGeo& gout,
                                   const void* tmap_in, const void* tmap_out, cudaStream_t s);
 
