@@ -69,9 +69,9 @@ struct OutFold {
 // Shared memory, in order: three L x W tile buffers (the TMA tile, then the
 // A operands over it), B hi / lo, the padded twiddle table, the output
 // layout's part/index table of the L rows (per CTA), two row-offset tables
-// (tiles i and i-1), three folds (one per tile buffer: the fold of tile i is
-// written before the barrier that ends the epilogue of tile i-2), per-column
-// maxima and unscale factors
+// (tiles i and i-1), three folds (one per tile buffer: the fold of tile i+1
+// is written in iteration i, after the barrier that follows the epilogue of
+// tile i-2), per-column maxima and unscale factors
 // (two tiles), six mbarriers (three copy barriers, two MMA barriers, spare)
 // and the tensor-memory slot.
 template <int L, int W>
@@ -199,7 +199,11 @@ __global__ void __launch_bounds__(W * 16, 1)
   };
 
   const int64_t tile0 = blockIdx.x;
-  if (tid == 0 && tile0 < ntiles) issue_load(tile0, tiles, &bars[0]);
+  if (tid == 0 && tile0 < ntiles) {
+    issue_load(tile0, tiles, &bars[0]);
+    fold_tile(tile0, 0);
+  }
+  __syncthreads();
   int it = 0, b = 0;   // b = it % 3
   int issued = 0;      // MMA groups committed (tiles 0 .. issued-1)
   int waited = 0;      // MMA commits waited for (tiles 0 .. waited-1)
@@ -212,8 +216,7 @@ __global__ void __launch_bounds__(W * 16, 1)
     // the copy of tile it+1 goes into the buffer of tile it-2, whose A
     // operands were consumed by MMAs waited for in iteration it-1
     if (tid == 0 && next < ntiles) issue_load(next, tiles + bn * BUF, &bars[bn]);
-    if (tid == 0) fold_tile(tile, b);
-    else if (tid == 32 && FMT == 0) {
+    if (tid == 32 && FMT == 0) {
       for (int c = 0; c < W; ++c) s_max[(k ^ 1) * W + c] = 0;  // tile it+1's maxima
     }
     const bool ok = mbar_wait(&bars[b], (it / 3) & 1, a.wait_limit);
@@ -245,7 +248,10 @@ __global__ void __launch_bounds__(W * 16, 1)
       m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));  // the lane of the same column
       if (lane < 16) atomicMax(&s_max[k * W + cx], __float_as_int(m));  // magnitudes: int order = float order
     }
-    __syncthreads();  // S1: the tile is read (A may overwrite it), the maxima and the fold are complete
+    __syncthreads();  // S1: the tile is read (A may overwrite it), the maxima are complete
+    // the next tile's output fold, by one thread of warp 1 while the others
+    // fill this tile's row table (folded one iteration ago)
+    if (tid == 32 && next < ntiles) fold_tile(next, bn);
     {
       const OutFold& f = s_fold[b];
       int* rout = s_rout + k * L;
