@@ -22,8 +22,10 @@
 // writes its A operands over the tile's own buffer and issues its MMAs into
 // one of two tensor-memory accumulators, then reads back the accumulator of
 // tile i-1 (whose MMAs ran meanwhile) and stores it straight to global
-// memory through a per-tile row table of the output layout (the scatter of
-// the redistribution); the TMA copy of tile i+1 is in flight all along.  No
+// memory (the scatter of the redistribution): in an equal-block layout an
+// output row's element offset is affine in its rank part and local index,
+// so every thread computes its rows' offsets from the tile geometry; the
+// TMA copy of tile i+1 is in flight all along.  No
 // tile buffer waits for a store, so three buffers give every load a whole
 // iteration of lead.  Four MMA groups of M = 128 rows, N = 32, K = 32 (two
 // K = 16 steps, three products each) per tile, issued by one thread and
@@ -58,31 +60,54 @@ __device__ __forceinline__ uint32_t op_off(int row, int k) {
 // indices jt k1 for two consecutive jt, so stride-k1 patterns spread out.
 __device__ __forceinline__ int tws(int i) { return i + (i >> 4); }
 
-// The output fold of a tile (see TileRows): rank part base, head, prod and
-// tail of the C-order index, and the split of the FFT axis (q, r).
-struct OutFold {
-  int64_t base, head, prod, tail;
-  int q, r;
-  int2 blk;
+// Element offsets of a tile's rows in an equal-block output layout (the
+// 5-D view of TmaGeo): rank r holds its (n0, n1, n2) block at r x local, and
+// global index g of axis m lies in rank part g / n[m] (rank stride rmul[m])
+// at local index g % n[m] when that axis is cut.  Row n of the tile (global
+// index n of the FFT axis `ax`) is at base + part(n) + col, with base fixed
+// by the tile's outer index and column block.
+struct OutRows {
+  int64_t base, local, sa;  // tile base, elements per rank, local stride of the FFT axis
+  int na, rma, cut;         // local extent of the FFT axis, its rank stride, whether it is cut
+  __device__ __forceinline__ OutRows(const TmaGeo& G, int ax, int tax, int64_t o, int col0) {
+    local = (int64_t)G.n[0] * G.n[1] * G.n[2];
+    const int64_t st[3] = {(int64_t)G.n[1] * G.n[2], (int64_t)G.n[2], 1};
+    const int64_t gi[3] = {tax == 0 ? o : 0, tax == 1 ? o : 0, (int64_t)col0};
+    int64_t rank = 0, idx = 0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      if (m == ax) continue;
+      int64_t g = gi[m];
+      if (G.cut[m]) {
+        const int64_t p = g / G.n[m];
+        rank += p * G.rmul[m];
+        g -= p * G.n[m];
+      }
+      idx += g * st[m];
+    }
+    base = rank * local + idx;
+    sa = (ax == 0) ? st[0] : (ax == 1) ? st[1] : 1;
+    na = G.n[ax];
+    rma = G.rmul[ax];
+    cut = G.cut[ax];
+  }
+  __device__ __forceinline__ int64_t row(int n) const {
+    if (!cut) return base + (int64_t)n * sa;
+    const int p = n / na;
+    return base + (int64_t)p * rma * local + (int64_t)(n - p * na) * sa;
+  }
 };
 
 // Shared memory, in order: three L x W tile buffers (the TMA tile, then the
-// A operands over it), B hi / lo, the padded twiddle table, the output
-// layout's part/index table of the L rows (per CTA), two row-offset tables
-// (tiles i and i-1), three folds (one per tile buffer: the fold of tile i+1
-// is written in iteration i, after the barrier that follows the epilogue of
-// tile i-2), per-column maxima and unscale factors
-// (two tiles), six mbarriers (three copy barriers, two MMA barriers, spare)
-// and the tensor-memory slot.
+// A operands over it), B hi / lo, the padded twiddle table, per-column
+// maxima and unscale factors (two tiles), six mbarriers (three copy
+// barriers, two MMA barriers, spare) and the tensor-memory slot.
 template <int L, int W>
 struct TcSmem {
   static constexpr size_t tiles = 0;
   static constexpr size_t b = tiles + 3 * (size_t)L * W * sizeof(float2);
   static constexpr size_t tw = b + 2 * kBBytes;
-  static constexpr size_t rp = tw + (L + L / 16) * sizeof(float2);
-  static constexpr size_t rout = rp + L * sizeof(uint32_t);
-  static constexpr size_t fold = rout + 2 * L * sizeof(int);
-  static constexpr size_t smax = fold + 3 * sizeof(OutFold);
+  static constexpr size_t smax = tw + (L + L / 16) * sizeof(float2);
   static constexpr size_t unscale = smax + 2 * W * sizeof(int);
   static constexpr size_t bars = (unscale + 2 * W * sizeof(float) + 7) / 8 * 8;
   static constexpr size_t slot = bars + 6 * sizeof(uint64_t);
@@ -91,7 +116,8 @@ struct TcSmem {
 
 template <int L, int E, int W, int FMT>
 __global__ void __launch_bounds__(W * 16, 1)
-    k_strided_tma_tc(const StridedArgs a, const TmaGeo gin, const __grid_constant__ CUtensorMap tin) {
+    k_strided_tma_tc(const StridedArgs a, const TmaGeo gin, const TmaGeo gout,
+                     const __grid_constant__ CUtensorMap tin) {
   static_assert(L == 16 * E && W * E == kRows, "tile = 512 sub-transforms of 16 points");
   static_assert((size_t)L * W * sizeof(float2) >= 2 * kOpBytes, "A fits in a tile buffer");
   using SM = TcSmem<L, W>;
@@ -103,9 +129,6 @@ __global__ void __launch_bounds__(W * 16, 1)
   uint8_t* b_hi = smraw + SM::b;
   uint8_t* b_lo = b_hi + kBBytes;
   float2* s_tw = reinterpret_cast<float2*>(smraw + SM::tw);
-  uint32_t* s_rp = reinterpret_cast<uint32_t*>(smraw + SM::rp);
-  int* s_rout = reinterpret_cast<int*>(smraw + SM::rout);           // [2][L]
-  OutFold* s_fold = reinterpret_cast<OutFold*>(smraw + SM::fold);   // [3], by tile buffer
   int* s_max = reinterpret_cast<int*>(smraw + SM::smax);            // [2][W] column maxima (float bits)
   float* s_unscale = reinterpret_cast<float*>(smraw + SM::unscale); // [2][W] factors 2^-s
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw + SM::bars);   // [0..2] copies, [3..4] MMA
@@ -126,13 +149,7 @@ __global__ void __launch_bounds__(W * 16, 1)
     fence_mbar_init();
   }
   build_dft16_operand<FMT>(b_hi, b_lo, kLBO, kSBO, a.tw, L, tid, NT);
-  for (int i = tid; i < L; i += NT) {
-    s_tw[tws(i)] = __ldg(&a.tw[i]);
-    // part and index of row i along the FFT axis in the output layout
-    int64_t c = 0, l = i, n = a.lout.N[a.axis];
-    if (a.lout.Mx[a.axis] > 1) locate(a.lout.N[a.axis], a.lout.Mx[a.axis], i, c, l, n);
-    s_rp[i] = ((uint32_t)c << 16) | (uint32_t)l;
-  }
+  for (int i = tid; i < L; i += NT) s_tw[tws(i)] = __ldg(&a.tw[i]);
   if (tid < 2 * W) s_max[tid] = 0;
   if (warp == 0) {
     tmem_alloc(tmem_slot, kTmemCols);
@@ -156,27 +173,13 @@ __global__ void __launch_bounds__(W * 16, 1)
       tma_load_5d(dst + (size_t)k * gin.rows_per_op * W, &tin, bar, c);
     }
   };
-  // the output rows of tile t folded by one thread (slot k)
-  auto fold_tile = [&](int64_t t, int k) {
+  // accumulator of tile j read back from tensor memory and stored
+  auto epilogue = [&](int j, int64_t t) {
+    const int k = j & 1;
     int64_t o;
     int2 blk;
     tile_place(a, t, o, blk);
-    const TileRows tr(a, a.lout, StridedTilePos(a, o, blk));
-    OutFold& f = s_fold[k];
-    f.base = tr.base;
-    f.head = tr.head;
-    f.prod = tr.prod;
-    f.tail = tr.tail;
-    const uint32_t N = (uint32_t)tr.N, M = (uint32_t)tr.M;
-    f.q = (int)(N / M);
-    f.r = (int)(N - (N / M) * M);
-    f.blk = blk;
-  };
-  // accumulator of tile j read back from tensor memory and stored
-  auto epilogue = [&](int j) {
-    const int k = j & 1;
-    const OutFold& f = s_fold[j % 3];
-    const int* rout = s_rout + k * L;
+    const OutRows rows(gout, a.axis, tax, o, blk.x);
     const uint32_t acc = tmem + (uint32_t)k * kAccCols;
 #pragma unroll
     for (int g = warp >> 2; g < 4; g += NW / 4) {
@@ -187,23 +190,19 @@ __global__ void __launch_bounds__(W * 16, 1)
       const int R = 128 * g + 32 * (warp & 3) + lane;
       const int k1 = R / W, c = R % W;
       const float fs = (FMT == 0) ? a.scale * s_unscale[k * W + c] : a.scale;
-      if (c < f.blk.y) {
+      if (c < blk.y) {
 #pragma unroll
         for (int k2 = 0; k2 < 16; ++k2) {
           float2 y = make_float2(r[2 * k2] * fs, r[2 * k2 + 1] * fs);
           if (inv) y.y = -y.y;
-          a.out[rout[k1 + E * k2] + c] = y;
+          a.out[rows.row(k1 + E * k2) + c] = y;
         }
       }
     }
   };
 
   const int64_t tile0 = blockIdx.x;
-  if (tid == 0 && tile0 < ntiles) {
-    issue_load(tile0, tiles, &bars[0]);
-    fold_tile(tile0, 0);
-  }
-  __syncthreads();
+  if (tid == 0 && tile0 < ntiles) issue_load(tile0, tiles, &bars[0]);
   int it = 0, b = 0;   // b = it % 3
   int issued = 0;      // MMA groups committed (tiles 0 .. issued-1)
   int waited = 0;      // MMA commits waited for (tiles 0 .. waited-1)
@@ -249,18 +248,6 @@ __global__ void __launch_bounds__(W * 16, 1)
       if (lane < 16) atomicMax(&s_max[k * W + cx], __float_as_int(m));  // magnitudes: int order = float order
     }
     __syncthreads();  // S1: the tile is read (A may overwrite it), the maxima are complete
-    // the next tile's output fold, by one thread of warp 1 while the others
-    // fill this tile's row table (folded one iteration ago)
-    if (tid == 32 && next < ntiles) fold_tile(next, bn);
-    {
-      const OutFold& f = s_fold[b];
-      int* rout = s_rout + k * L;
-      for (int i = tid; i < L; i += NT) {
-        const int c = (int)(s_rp[i] >> 16), l = (int)(s_rp[i] & 0xFFFF);
-        const int64_t n = f.q + (c < f.r ? 1 : 0);
-        rout[i] = (int)(a.lout.offset[f.base + c * a.lout.rs[a.axis]] + (f.head * n + l) * f.prod + f.tail);
-      }
-    }
     float sc = 1.f;
     if constexpr (FMT == 0) {
       const int sh = fp16_range_shift(__int_as_float(s_max[k * W + cx]));
@@ -279,7 +266,7 @@ __global__ void __launch_bounds__(W * 16, 1)
     }
     fence_proxy_async();
     tc_fence_before();
-    __syncthreads();  // S2: A, the row table and the scale factors of tile it are complete
+    __syncthreads();  // S2: A and the scale factors of tile it are complete
     tc_fence_after();
     if (tid == 0) {
       const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
@@ -313,7 +300,7 @@ __global__ void __launch_bounds__(W * 16, 1)
       }
       ++waited;
       tc_fence_after();
-      epilogue(j);
+      epilogue(j, tile - gridDim.x);
       tc_fence_before();
     }
   }
@@ -326,7 +313,7 @@ __global__ void __launch_bounds__(W * 16, 1)
     } else {
       ++waited;
       tc_fence_after();
-      epilogue(j);
+      epilogue(j, tile0 + (int64_t)j * gridDim.x);
     }
   }
   // MMAs committed but never waited for (a wait gave up): wait for their
@@ -349,7 +336,8 @@ __global__ void __launch_bounds__(W * 16, 1)
 }
 
 template <int L, int E, int W, int FMT>
-cudaError_t run_tc_strided(const StridedArgs& a, const TmaGeo& gi, const CUtensorMap& ti, cudaStream_t s) {
+cudaError_t run_tc_strided(const StridedArgs& a, const TmaGeo& gi, const TmaGeo& go, const CUtensorMap& ti,
+                           cudaStream_t s) {
   auto kern = k_strided_tma_tc<L, E, W, FMT>;
   constexpr size_t smem = TcSmem<L, W>::total;
   static_assert(smem <= 227 * 1024, "shared memory of one CTA");
@@ -362,28 +350,26 @@ cudaError_t run_tc_strided(const StridedArgs& a, const TmaGeo& gi, const CUtenso
   const int64_t ntiles = a.nouter * a.ncolblocks;
   const int64_t grid = ntiles < slots ? ntiles : slots;
   if (grid < 1) return cudaSuccess;
-  kern<<<(unsigned)grid, W * 16, smem, s>>>(a, gi, ti);
+  kern<<<(unsigned)grid, W * 16, smem, s>>>(a, gi, go, ti);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_strided_supported(int L, int E, int W, int64_t nelems) {
-  // the row tables hold 32-bit element offsets
-  if (nelems >= (int64_t(1) << 31)) return false;
+  (void)nelems;  // offsets are 64-bit
   return (L == 512 && E == 32 && W == 16) || (L == 256 && E == 16 && W == 32);
 }
 
 cudaError_t launch_strided_tma_tc(const StridedArgs& a, int E, int precision, const TmaGeo& gi, const TmaGeo& go,
                                   const void* tmap_in, const void* tmap_out, cudaStream_t s) {
-  (void)go;
-  (void)tmap_out;  // the results are stored through the output layout's row table
+  (void)tmap_out;  // the results are stored with plain stores at offsets from the output geometry
   const CUtensorMap& ti = *static_cast<const CUtensorMap*>(tmap_in);
   const bool fp16 = precision == 2;
   if (a.ap.L == 512 && E == 32 && a.W == 16)
-    return fp16 ? run_tc_strided<512, 32, 16, 0>(a, gi, ti, s) : run_tc_strided<512, 32, 16, 1>(a, gi, ti, s);
+    return fp16 ? run_tc_strided<512, 32, 16, 0>(a, gi, go, ti, s) : run_tc_strided<512, 32, 16, 1>(a, gi, go, ti, s);
   if (a.ap.L == 256 && E == 16 && a.W == 32)
-    return fp16 ? run_tc_strided<256, 16, 32, 0>(a, gi, ti, s) : run_tc_strided<256, 16, 32, 1>(a, gi, ti, s);
+    return fp16 ? run_tc_strided<256, 16, 32, 0>(a, gi, go, ti, s) : run_tc_strided<256, 16, 32, 1>(a, gi, go, ti, s);
   return cudaErrorInvalidValue;
 }
 
