@@ -43,6 +43,20 @@ Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
       // on axis 0 as well (0.395 vs 0.588 ms)
       s.tma_outer_fastest = axis == 0 && Wt * sizeof(float2) >= 128;
     }
+    // tensor-core plans: the tensor-core TMA variant of this length, with its
+    // own tile width (and so its own geometry and column blocks)
+    int Ec = 0, Wc = 0;
+    s.tc = p->precision != TFFT_FP32 && p->use_tma && ap.spec &&
+           tc_strided_variant(s.L, tuned_width(s.L, nullptr, "TFFT_TC_W"), Ec, Wc) &&
+           tma_geo(p, lin, axis, Wc, s.tc_gin) && tma_geo(p, lout, axis, Wc, s.tc_gout);
+    if (s.tc) {
+      s.tc_E = Ec;
+      s.tc_W = Wc;
+      auto cbc = get_colblocks(p, lin, lout, Wc);
+      s.tc_cb_off = cbc.first;
+      s.tc_ncb = cbc.second;
+      s.tc_outer_fastest = axis == 0 && Wc * sizeof(float2) >= 128;
+    }
   }
   return s;
 }
@@ -196,7 +210,20 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.status = reinterpret_cast<int*>(p->d_state);
     a.wait_limit = p->wait_limit;
     bool done = false;
-    if (s.tma) {
+    if (s.tc) {
+      alignas(64) CUtensorMap ti, to;
+      if (encode_stage_map(p, s.tc_gin, s.axis, s.tc_W, in, &ti) &&
+          encode_stage_map(p, s.tc_gout, s.axis, s.tc_W, out, &to)) {
+        StridedArgs at = a;
+        at.W = s.tc_W;
+        at.colblocks = reinterpret_cast<const int2*>(p->d_state + s.tc_cb_off);
+        at.ncolblocks = s.tc_ncb;
+        at.outer_fastest = s.tc_outer_fastest ? 1 : 0;
+        e = launch_strided_tma_tc(at, s.tc_E, p->precision, s.tc_gin, s.tc_gout, &ti, &to, st);
+        done = true;
+      }
+    }
+    if (!done && s.tma) {
       alignas(64) CUtensorMap ti, to;
       if (encode_stage_map(p, s.gin, s.axis, s.tma_W, in, &ti) &&
           encode_stage_map(p, s.gout, s.axis, s.tma_W, out, &to)) {
@@ -205,10 +232,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
         at.colblocks = reinterpret_cast<const int2*>(p->d_state + s.tma_cb_off);
         at.ncolblocks = s.tma_ncb;
         at.outer_fastest = s.tma_outer_fastest ? 1 : 0;
-        if (p->precision != TFFT_FP32 && tc_strided_supported(s.L, s.tma_E, s.tma_W, p->nelems))
-          e = launch_strided_tma_tc(at, s.tma_E, p->precision, s.gin, s.gout, &ti, &to, st);
-        else
-          e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
+        e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
         done = true;
       }
     }
@@ -396,10 +420,8 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
       elems = s.box_elems;
     } else {
       const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
-      const bool tma = s.kind == S_STRIDED && s.tma;
-      const bool tc = p->precision != TFFT_FP32 &&
-                      ((s.kind == S_CONTIG && tc_supported(ap.L)) ||
-                       (tma && tc_strided_supported(s.L, s.tma_E, s.tma_W, p->nelems)));
+      const bool tma = s.kind == S_STRIDED && (s.tma || s.tc);
+      const bool tc = p->precision != TFFT_FP32 && ((s.kind == S_CONTIG && tc_supported(ap.L)) || s.tc);
       nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
            (tma ? "_tma" : "") + (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : "") +
            (ap.blue_m ? "_bluestein_L" + std::to_string(ap.L)

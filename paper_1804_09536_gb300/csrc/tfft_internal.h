@@ -264,9 +264,11 @@ cudaError_t launch_batch(const BatchArgs& b, int grid, cudaStream_t s);
 bool tc_supported(int L);
 cudaError_t launch_contig_tc(const ContigArgs& a, int precision, cudaStream_t s);
 
-// Tensor-core strided TMA passes (tfft_tc_strided.cu): lengths 512 (E = 32,
-// W = 16) and 256 (E = 16, W = 32), the last radix-16 stage on tcgen05.
-bool tc_strided_supported(int L, int E, int W, int64_t nelems);
+// Tensor-core strided TMA passes (tfft_tc_strided.cu): lengths 512 (E = 32)
+// and 256 (E = 16), the last radix-16 stage on tcgen05; tc_strided_variant
+// gives the first-stage radix and tile width of the compiled variant of
+// length L with width want_W if there is one, else the default.
+bool tc_strided_variant(int L, int want_W, int& E, int& W);
 cudaError_t launch_strided_tma_tc(const StridedArgs& a, int E, int precision, const TmaGeo& gin, const TmaGeo& gout,
                                   const void* tmap_in, const void* tmap_out, cudaStream_t s);
 

@@ -80,6 +80,13 @@ struct Step {
   int64_t tma_ncb = 0;
   bool tma_outer_fastest = false;  // tile order of the TMA pass
   TmaGeo gin{}, gout{};
+  // tensor-core TMA pass (TFFT_TC_* plans): its variant, column blocks and geometry
+  bool tc = false;
+  int tc_E = 0, tc_W = 0;
+  size_t tc_cb_off = 0;
+  int64_t tc_ncb = 0;
+  bool tc_outer_fastest = false;
+  TmaGeo tc_gin{}, tc_gout{};
 };
 
 struct ExchangeBoxes {  // one adjacent-stage exchange
@@ -184,7 +191,7 @@ Step box_step(const BoxList& L);
 int split_rows(int L);
 bool tma_geo(tfft_plan p, int stage, int axis, int W, TmaGeo& G);
 bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void* base, CUtensorMap* map);
-int tuned_width(int L, int* E = nullptr);
+int tuned_width(int L, int* E = nullptr, const char* var = "TFFT_TMA_W");
 
 // ---- pass lists and launches (tfft_exec.cpp)
 Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign);

@@ -106,10 +106,10 @@ bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void*
 
 // Tile width (and optionally elements per thread) requested for the strided
 // TMA pass of length L by the environment, TFFT_TMA_W="512:8:16,256:32"
-// (used when tuning); 0 when not given.
-int tuned_width(int L, int* E) {
+// (TFFT_TC_W for the tensor-core passes; used when tuning); 0 when not given.
+int tuned_width(int L, int* E, const char* var) {
   if (E) *E = 0;
-  const char* env = std::getenv("TFFT_TMA_W");
+  const char* env = std::getenv(var);
   if (!env) return 0;
   std::string v(env);
   size_t pos = 0;
