@@ -43,6 +43,14 @@ Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign) {
       // on axis 0 as well (0.395 vs 0.588 ms)
       s.tma_outer_fastest = axis == 0 && Wt * sizeof(float2) >= 128;
     }
+    // uneven blocks: an in-place pass along axis 0 can still run TMA-staged
+    // tiles over the layout's rank groups
+    if (!s.tma && p->use_tma && ap.spec && lin == lout && axis == 0 &&
+        tma_strided_variant(s.L, wantW, wantE, Et, Wt) && rank_groups(p, lin, s.L, Wt, s.rg, s.rgh)) {
+      s.tma_groups = true;
+      s.tma_E = Et;
+      s.tma_W = Wt;
+    }
     // tensor-core plans: the tensor-core TMA variant of this length, with its
     // own tile width (and so its own geometry and column blocks)
     int Ec = 0, Wc = 0;
@@ -236,6 +244,23 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
         done = true;
       }
     }
+    if (!done && s.tma_groups) {
+      alignas(64) CUtensorMap ti[kMaxRankGroups], to[kMaxRankGroups];
+      const void* pin[kMaxRankGroups];
+      const void* pout[kMaxRankGroups];
+      bool ok = true;
+      for (int k = 0; k < s.rg.ngroups && ok; ++k) {
+        ok = encode_group_map(s.rgh[k], s.L, s.tma_W, in, &ti[k]) && encode_group_map(s.rgh[k], s.L, s.tma_W, out, &to[k]);
+        pin[k] = &ti[k];
+        pout[k] = &to[k];
+      }
+      if (ok) {
+        StridedArgs at = a;
+        at.W = s.tma_W;
+        e = launch_strided_tma_groups(at, s.tma_E, s.rg, pin, pout, st);
+        done = true;
+      }
+    }
     if (!done && a.ap.blue_m) {
       e = launch_strided_blue(a, blue_args(p, s.L), st);
       done = true;
@@ -420,10 +445,11 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
       elems = s.box_elems;
     } else {
       const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
-      const bool tma = s.kind == S_STRIDED && (s.tma || s.tc);
+      const bool tma = s.kind == S_STRIDED && (s.tma || s.tc || s.tma_groups);
       const bool tc = p->precision != TFFT_FP32 && ((s.kind == S_CONTIG && tc_supported(ap.L)) || s.tc);
       nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
-           (tma ? "_tma" : "") + (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : "") +
+           (tma ? "_tma" : "") + (s.kind == S_STRIDED && s.tma_groups && !s.tc ? "_groups" : "") +
+           (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : "") +
            (ap.blue_m ? "_bluestein_L" + std::to_string(ap.L)
                       : ap.spec ? "_L" + std::to_string(ap.L)
                                 : ap.E == 0 ? std::string("_generic") : "_E" + std::to_string(ap.E));

@@ -181,6 +181,22 @@ struct TmaGeo {
   int rmul[3];
 };
 
+// Rank groups of an uneven stage layout seen by the TMA passes along its
+// leading, uncut axis (in place): the ranks that hold blocks of one shape,
+// whose offsets are affine in their grid coordinates, described by one
+// tensor map each (see the TMA pass).  Tiles are numbered group after group:
+// group g has first[g + 1] - first[g] = (its ranks) x nblk[g] tiles, a rank
+// r = r1 + ext1[g] r0 of the group holding nblk[g] blocks of `width` merged
+// inner columns.
+constexpr int kMaxRankGroups = 4;
+struct RankGroupGeo {
+  int ngroups;
+  int width;
+  int64_t first[kMaxRankGroups + 1];
+  int nblk[kMaxRankGroups];
+  int ext1[kMaxRankGroups];
+};
+
 // Copy of rectangular boxes: each box has up to MAXD extents, a source and a
 // destination base offset and per-axis strides (the innermost stride is 1 on
 // both sides).  This is the all-to-all of subarray types of Alg. 3 on the
@@ -313,5 +329,9 @@ cudaError_t launch_real_spec(const RealArgs& a, cudaStream_t s);
 bool tma_strided_variant(int L, int want_W, int want_E, int& E, int& W);
 cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gin, const TmaGeo& gout,
                                const void* tmap_in, const void* tmap_out, cudaStream_t s);
+// The same passes over the rank groups of an uneven layout (in place along
+// the leading axis): tmaps_in / tmaps_out hold g.ngroups host CUtensorMaps each.
+cudaError_t launch_strided_tma_groups(const StridedArgs& a, int E, const RankGroupGeo& g, const void* const* tmaps_in,
+                                      const void* const* tmaps_out, cudaStream_t s);
 
 }  // namespace tfft

@@ -54,6 +54,15 @@ enum StepKind { S_CONTIG, S_STRIDED, S_BOX, S_REAL };
 constexpr int kAdjoint = 2;  // key of the adjoint's step list
 enum BufId { BUF_IN, BUF_OUT, BUF_W0, BUF_W1 };
 
+// One rank group of an uneven stage layout (see RankGroupGeo): the element
+// offset of its first rank, the merged extent of the axes after axis 0, the
+// offsets between consecutive ranks along its two rank dimensions and their
+// extents.
+struct RankGroupH {
+  int64_t base = 0, inner = 0, s1 = 0, s0 = 0;
+  int ext1 = 1, ext0 = 1;
+};
+
 struct Step {
   StepKind kind;
   int src = BUF_IN, dst = BUF_OUT;
@@ -87,6 +96,10 @@ struct Step {
   int64_t tc_ncb = 0;
   bool tc_outer_fastest = false;
   TmaGeo tc_gin{}, tc_gout{};
+  // TMA pass over the rank groups of an uneven layout (in place along axis 0)
+  bool tma_groups = false;
+  RankGroupGeo rg{};
+  std::vector<RankGroupH> rgh;
 };
 
 struct ExchangeBoxes {  // one adjacent-stage exchange
@@ -192,6 +205,8 @@ int split_rows(int L);
 bool tma_geo(tfft_plan p, int stage, int axis, int W, TmaGeo& G);
 bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void* base, CUtensorMap* map);
 int tuned_width(int L, int* E = nullptr, const char* var = "TFFT_TMA_W");
+bool rank_groups(tfft_plan p, int stage, int L, int W, RankGroupGeo& G, std::vector<RankGroupH>& groups);
+bool encode_group_map(const RankGroupH& H, int L, int W, const void* base, CUtensorMap* map);
 
 // ---- pass lists and launches (tfft_exec.cpp)
 Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign);

@@ -13,6 +13,16 @@
 // buffered three deep: the copy of tile i+1 runs while tile i is
 // transformed and the store of tile i-1 drains.
 //
+// The same kernel also runs in-place passes along the leading axis of layouts
+// whose ranks do NOT hold equal blocks (an uneven split of Eq. decompose):
+// each rank's local array is then a 2-D array (L rows x the product of the
+// other extents), the ranks with equal blocks form at most four groups whose
+// offsets are affine in the rank coordinates, and one tensor map per group
+// describes them.  A tile is W consecutive elements of that merged inner
+// extent (columns of independent lines) over all L rows of one rank; the
+// last tile of a rank may be partial -- the copy fills the missing columns
+// with zeros and the store skips them.
+//
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // TFFT_DEVICE_ETIMEOUT in the plan's status word and leaves.
 #include "tfft_tiles.cuh"
@@ -30,10 +40,77 @@ __host__ __device__ constexpr size_t strided_tma_smem(int L, int W) {
   return 3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t);
 }
 
-template <int L, int E, int W, int... Rs>
+// Tiles of the equal-block view: (outer index, column block), gathered and
+// scattered through the 5-D TmaGeo views of the input and output layouts.
+struct BlockTiles {
+  CUtensorMap tin, tout;
+  TmaGeo gin, gout;
+  __device__ __forceinline__ int64_t ntiles(const StridedArgs& a) const { return a.nouter * a.ncolblocks; }
+  template <int W>
+  __device__ __forceinline__ void load(const StridedArgs& a, int64_t tile, float2* dst, uint64_t* bar) const {
+    int64_t o;
+    int2 blk;
+    tile_place(a, tile, o, blk);
+    const int tax = (a.oax0 >= 0) ? a.oax0 : -1;  // the outer axis (d == 3)
+    for (int k = 0; k < gin.nops; ++k) {
+      int c[5];
+      tile_coords(gin, a.axis, k, blk.x, o, tax, c);
+      tma_load_5d(dst + (size_t)k * gin.rows_per_op * W, &tin, bar, c);
+    }
+  }
+  template <int W>
+  __device__ __forceinline__ void store(const StridedArgs& a, int64_t tile, const float2* src) const {
+    int64_t o;
+    int2 blk;
+    tile_place(a, tile, o, blk);
+    const int tax = (a.oax0 >= 0) ? a.oax0 : -1;
+    for (int k = 0; k < gout.nops; ++k) {
+      int c[5];
+      tile_coords(gout, a.axis, k, blk.x, o, tax, c);
+      tma_store_5d(&tout, src + (size_t)k * gout.rows_per_op * W, c);
+    }
+  }
+};
+
+// Tiles of the rank-group view (uneven blocks, in-place leading-axis pass):
+// group g covers tiles [first[g], first[g + 1]), nblk[g] column blocks per
+// rank, its ranks numbered r1 + ext1[g] r0; its tensor maps view it as
+// [inner][rows / a][a... ] = [inner][a][L / a][ext1][ext0] (a = rows of the
+// inner row box, at most 256).
+struct RankGroupTiles {
+  CUtensorMap tin[kMaxRankGroups], tout[kMaxRankGroups];
+  RankGroupGeo geo;
+  __device__ __forceinline__ int64_t ntiles(const StridedArgs&) const { return geo.first[geo.ngroups]; }
+  __device__ __forceinline__ int place(int64_t tile, int (&c)[5]) const {
+    int g = 0;
+    while (g + 1 < geo.ngroups && tile >= geo.first[g + 1]) ++g;
+    const int64_t local = tile - geo.first[g];
+    const int64_t rank = local / geo.nblk[g];
+    const int blk = (int)(local - rank * geo.nblk[g]);
+    c[0] = blk * geo.width;
+    c[1] = 0;
+    c[2] = 0;
+    c[3] = (int)(rank % geo.ext1[g]);
+    c[4] = (int)(rank / geo.ext1[g]);
+    return g;
+  }
+  template <int W>
+  __device__ __forceinline__ void load(const StridedArgs&, int64_t tile, float2* dst, uint64_t* bar) const {
+    int c[5];
+    const int g = place(tile, c);
+    tma_load_5d(dst, &tin[g], bar, c);
+  }
+  template <int W>
+  __device__ __forceinline__ void store(const StridedArgs&, int64_t tile, const float2* src) const {
+    int c[5];
+    const int g = place(tile, c);
+    tma_store_5d(&tout[g], src, c);
+  }
+};
+
+template <int L, int E, int W, class Geo, int... Rs>
 __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1024 ? 2 : 1)
-    k_strided_tma(const StridedArgs a, const TmaGeo gin, const TmaGeo gout,
-                  const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout) {
+    k_strided_tma(const StridedArgs a, const __grid_constant__ Geo geo) {
   constexpr int T = L / E, NST = sizeof...(Rs);
   constexpr int WP = (W % 16 == 0) ? W : W + 1;  // exchange pitch (bank-conflict padding)
   constexpr int BUF = L * (W + 1);
@@ -44,8 +121,7 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
   const int cx = threadIdx.x;
   const int tid = threadIdx.y * W + cx;
   const bool inv = a.sign > 0;
-  const int64_t ntiles = a.nouter * a.ncolblocks;
-  const int tax = (a.oax0 >= 0) ? a.oax0 : -1;  // the outer axis (d == 3)
+  const int64_t ntiles = geo.ntiles(a);
   const uint32_t tile_bytes = (uint32_t)(L * W * sizeof(float2));
 
   if (tid == 0) {
@@ -56,15 +132,8 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
   __syncthreads();
 
   auto issue_load = [&](int64_t tile, float2* dst, uint64_t* bar) {
-    int64_t o;
-    int2 blk;
-    tile_place(a, tile, o, blk);
     mbar_expect_tx(bar, tile_bytes);
-    for (int k = 0; k < gin.nops; ++k) {
-      int c[5];
-      tile_coords(gin, a.axis, k, blk.x, o, tax, c);
-      tma_load_5d(dst + (size_t)k * gin.rows_per_op * W, &tin, bar, c);
-    }
+    geo.template load<W>(a, tile, dst, bar);
   };
 
   int64_t tile = blockIdx.x;
@@ -138,14 +207,7 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
     fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
-      int64_t o;
-      int2 blk;
-      tile_place(a, tile, o, blk);
-      for (int k = 0; k < gout.nops; ++k) {
-        int c[5];
-        tile_coords(gout, a.axis, k, blk.x, o, tax, c);
-        tma_store_5d(&tout, cur + (size_t)k * gout.rows_per_op * W, c);
-      }
+      geo.template store<W>(a, tile, cur);
       bulk_commit();
     }
   }
@@ -166,10 +228,9 @@ int64_t persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
   return ntiles < g ? ntiles : g;
 }
 
-template <int L, int E, int W, int... Rs>
-cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo& go, const CUtensorMap& ti,
-                            const CUtensorMap& to, cudaStream_t s) {
-  auto kern = k_strided_tma<L, E, W, Rs...>;
+template <int L, int E, int W, class Geo, int... Rs>
+cudaError_t run_strided_tma(const StridedArgs& a, const Geo& geo, cudaStream_t s) {
+  auto kern = k_strided_tma<L, E, W, Geo, Rs...>;
   TFFT_ALLOW_SMEM(kern);
   if (attr != cudaSuccess) return attr;
   if (a.W != W) return cudaErrorInvalidValue;
@@ -178,10 +239,10 @@ cudaError_t run_strided_tma(const StridedArgs& a, const TmaGeo& gi, const TmaGeo
   static PerDevice<int64_t> slots_cache;
   const int64_t slots =
       slots_cache.get(current_device(), [&] { return persistent_grid(kern, threads, smem, int64_t(1) << 40); });
-  const int64_t ntiles = a.nouter * a.ncolblocks;
+  const int64_t ntiles = geo.ntiles(a);
   const int64_t grid = ntiles < slots ? ntiles : slots;
   if (grid < 1) return cudaSuccess;
-  kern<<<(unsigned)grid, dim3(W, L / E), smem, s>>>(a, gi, go, ti, to);
+  kern<<<(unsigned)grid, dim3(W, L / E), smem, s>>>(a, geo);
   return cudaGetLastError();
 }
 
@@ -220,11 +281,31 @@ bool tma_strided_variant(int L, int want_W, int want_E, int& E, int& W) {
 
 cudaError_t launch_strided_tma(const StridedArgs& a, int E, const TmaGeo& gi, const TmaGeo& go,
                                const void* tmap_in, const void* tmap_out, cudaStream_t s) {
-  const CUtensorMap& ti = *static_cast<const CUtensorMap*>(tmap_in);
-  const CUtensorMap& to = *static_cast<const CUtensorMap*>(tmap_out);
+  BlockTiles geo;
+  geo.tin = *static_cast<const CUtensorMap*>(tmap_in);
+  geo.tout = *static_cast<const CUtensorMap*>(tmap_out);
+  geo.gin = gi;
+  geo.gout = go;
 #define X(LL, EE, WW, ...)                   \
   if (a.ap.L == LL && E == EE && a.W == WW) \
-    return run_strided_tma<LL, EE, WW, __VA_ARGS__>(a, gi, go, ti, to, s);
+    return run_strided_tma<LL, EE, WW, BlockTiles, __VA_ARGS__>(a, geo, s);
+  TFFT_TMA_STRIDED(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_strided_tma_groups(const StridedArgs& a, int E, const RankGroupGeo& g, const void* const* tmaps_in,
+                                      const void* const* tmaps_out, cudaStream_t s) {
+  if (g.ngroups < 1 || g.ngroups > kMaxRankGroups || g.width != a.W) return cudaErrorInvalidValue;
+  RankGroupTiles geo;
+  for (int k = 0; k < g.ngroups; ++k) {
+    geo.tin[k] = *static_cast<const CUtensorMap*>(tmaps_in[k]);
+    geo.tout[k] = *static_cast<const CUtensorMap*>(tmaps_out[k]);
+  }
+  geo.geo = g;
+#define X(LL, EE, WW, ...)                   \
+  if (a.ap.L == LL && E == EE && a.W == WW) \
+    return run_strided_tma<LL, EE, WW, RankGroupTiles, __VA_ARGS__>(a, geo, s);
   TFFT_TMA_STRIDED(X)
 #undef X
   return cudaErrorInvalidValue;

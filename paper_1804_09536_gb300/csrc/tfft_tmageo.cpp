@@ -128,5 +128,99 @@ int tuned_width(int L, int* E, const char* var) {
   return 0;
 }
 
+// Rank groups of stage `stage` for an in-place TMA pass along axis 0 (held
+// whole in that stage) when its ranks do not all hold equal blocks.  Each
+// grid direction splits its axis into r parts of q + 1 and M - r parts of q
+// (Eq. decompose); the ranks of one size class per direction form a group.
+// A group qualifies when its ranks' blocks have one shape, its offsets are
+// affine in the rank coordinates, and every offset and the merged inner
+// extent are even (16-byte aligned rows for the tensor copies).
+bool rank_groups(tfft_plan p, int stage, int L, int W, RankGroupGeo& G, std::vector<RankGroupH>& groups) {
+  groups.clear();
+  if (p->g < 1 || p->g > 2 || p->d < 2) return false;
+  const LayoutH& S = p->st[stage];
+  if (S.owner[0] >= 0 || p->cshape[0] != L || (W & 1)) return false;
+  const int d = p->d;
+  // class ranges [lo, hi) of every grid direction
+  std::vector<std::pair<int, int>> cls[2];
+  for (int i = 0; i < p->g; ++i) {
+    int ax = -1;
+    for (int m = 0; m < d; ++m)
+      if (S.owner[m] == i) ax = m;
+    if (ax < 0) return false;
+    const int64_t M = p->grid[i], r = p->cshape[ax] % M;
+    if (r > 0) cls[i] = {{0, (int)r}, {(int)r, (int)M}};
+    else cls[i] = {{0, (int)M}};
+  }
+  if (p->g == 1) cls[1] = {{0, 1}};
+  const int64_t rs0 = p->rstride[0], rs1 = p->g == 2 ? p->rstride[1] : 0;
+  for (const auto& c0 : cls[0])
+    for (const auto& c1 : cls[1]) {
+      // the group's ranks: direction 0 in [c0), direction 1 in [c1)
+      auto rank_of = [&](int p0, int p1) { return (int)(p0 * rs0 + p1 * rs1); };
+      RankGroupH H;
+      const int r00 = rank_of(c0.first, c1.first);
+      int64_t inner = 1;
+      for (int m = 1; m < d; ++m) inner *= S.size[(size_t)r00 * d + m];
+      if (S.size[(size_t)r00 * d] != L || inner == 0) return false;
+      H.inner = inner;
+      H.base = S.offset[r00];
+      // ranks along direction 1 are the fastest group dimension (for a slab,
+      // direction 0 takes that place)
+      const int e1 = p->g == 2 ? c1.second - c1.first : c0.second - c0.first;
+      const int e0 = p->g == 2 ? c0.second - c0.first : 1;
+      H.ext1 = e1;
+      H.ext0 = e0;
+      auto rank_at = [&](int i1, int i0) {
+        return p->g == 2 ? rank_of(c0.first + i0, c1.first + i1) : rank_of(c0.first + i1, 0);
+      };
+      H.s1 = e1 > 1 ? S.offset[rank_at(1, 0)] - H.base : inner * L;
+      H.s0 = e0 > 1 ? S.offset[rank_at(0, 1)] - H.base : inner * L * e1;
+      for (int i0 = 0; i0 < e0; ++i0)
+        for (int i1 = 0; i1 < e1; ++i1) {
+          const int rk = rank_at(i1, i0);
+          for (int m = 0; m < d; ++m)
+            if (S.size[(size_t)rk * d + m] != S.size[(size_t)r00 * d + m]) return false;
+          if (S.offset[rk] != H.base + i1 * H.s1 + i0 * H.s0) return false;
+        }
+      if ((H.inner | H.base | H.s1 | H.s0) & 1) return false;
+      groups.push_back(H);
+    }
+  if (groups.empty() || (int)groups.size() > kMaxRankGroups) return false;
+  G = RankGroupGeo{};
+  G.ngroups = (int)groups.size();
+  G.width = W;
+  G.first[0] = 0;
+  for (int k = 0; k < G.ngroups; ++k) {
+    const RankGroupH& H = groups[k];
+    G.nblk[k] = (int)((H.inner + W - 1) / W);
+    G.ext1[k] = H.ext1;
+    G.first[k + 1] = G.first[k] + (int64_t)G.nblk[k] * H.ext1 * H.ext0;
+  }
+  return true;
+}
+
+// Tensor map of one rank group as [inner][a][L / a][ext1][ext0] complex64
+// elements (a = the rows of one box dimension, at most 256), box
+// W x a x L / a x 1 x 1: one tile is one copy each way.
+bool encode_group_map(const RankGroupH& H, int L, int W, const void* base, CUtensorMap* map) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const int a = L <= 256 ? L : split_rows(L);
+  if (a <= 0) return false;
+  const char* b = static_cast<const char*>(base) + H.base * 8;
+  cuuint64_t dims[5] = {(cuuint64_t)H.inner, (cuuint64_t)a, (cuuint64_t)(L / a), (cuuint64_t)H.ext1,
+                        (cuuint64_t)H.ext0};
+  cuuint64_t strides[4] = {(cuuint64_t)H.inner * 8, (cuuint64_t)H.inner * 8 * a, (cuuint64_t)H.s1 * 8,
+                           (cuuint64_t)H.s0 * 8};
+  cuuint32_t box[5] = {(cuuint32_t)W, (cuuint32_t)a, (cuuint32_t)(L / a), 1, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapL2promotion promo =
+      W * 8 >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<char*>(b), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 }  // namespace host
 }  // namespace tfft

@@ -121,6 +121,47 @@ def test_tma_and_plain_passes_agree(cuda_device, shape, grid):
     assert rel_l2(yt.cpu().numpy(), want) <= RTOL_FP32
 
 
+@pytest.mark.parametrize("shape,grid,kind", [((512, 64, 100), (2, 3), "c2c"),   # axis 2 split 34/33/33
+                                             ((64, 64, 64), (2, 4), "c2c"),    # equal blocks, 16-column ranks
+                                             ((96, 96, 96), (2, 4), "c2c"),
+                                             ((128, 64, 256), (2, 4), "r2c"),  # 129 complex split 33/32/32/32
+                                             ((64, 128, 512), (4, 8), "r2c"),  # the r2c pencil kind, 257 = 33 + 7 x 32
+                                             ((256, 32, 256), (8,), "r2c")])   # r2c slab, rows of 129
+def test_rank_group_tma_passes(cuda_device, shape, grid, kind):
+    """In-place passes along axis 0 of layouts without the equal-block 5-D view
+    (uneven splits, odd row lengths, ranks narrower than a tile) run TMA-staged
+    tiles over the layout's rank groups: same bits as the plain passes (equal
+    radices), and the oracle's result."""
+    from paper_1804_09536_gb300.plan import Plan
+    g = len(grid)
+    pt = Plan(shape, grid, kind=kind, device=cuda_device)
+    pp = Plan(shape, grid, kind=kind, device=cuda_device, tma=False)
+    names = [n for n, _ in pt.launch_info(-1)] + [n for n, _ in pt.launch_info(+1)]
+    assert sum("tma_groups" in n for n in names) == 2, names
+    if kind == "r2c":
+        x = inputs.normal_real(shape, seed=9).numpy()
+        want = dft.distributed_rfft_forward(R.scatter(x, grid, 0).astype(np.float64), shape, grid)
+        b0 = R.scatter(x, grid, 0)
+    else:
+        x = inputs.normal_complex(shape, seed=9).numpy()
+        b0 = R.scatter(x, grid, 0)
+        want = dft.distributed_forward(b0.astype(np.complex128), shape, grid)
+    yt = pt.forward(to_dev(b0, cuda_device))
+    yp = pp.forward(to_dev(b0, cuda_device))
+    zt = pt.inverse(yt.clone())
+    zp = pp.inverse(yp.clone())
+    torch.cuda.synchronize()
+    assert pt.device_status() == 0
+    assert rel_l2(yt.cpu().numpy(), want) <= RTOL_FP32
+    if 512 not in shape[:1]:
+        assert np.array_equal(bits(yt), bits(yp))
+        assert np.array_equal(bits(zt), bits(zp))
+    else:
+        assert rel_l2(yt.cpu().numpy(), yp.cpu().numpy()) <= 2e-6
+        assert rel_l2(zt.cpu().numpy(), zp.cpu().numpy()) <= 2e-6
+    assert rel_l2(zt.cpu().numpy(), b0) <= RTOL_FP32
+
+
 @pytest.mark.parametrize("shape,grid", [((32, 32, 32), (2, 2)), ((40, 48, 60), (3, 4))])
 def test_round_trip_and_destroyed_input(cuda_device, shape, grid):
     """App. A: backward(forward(x)) = x; without a workspace the input is scratch."""
