@@ -45,7 +45,7 @@ __host__ __device__ constexpr size_t strided_tma_smem(int L, int W) {
 struct BlockTiles {
   CUtensorMap tin, tout;
   TmaGeo gin, gout;
-  __device__ __forceinline__ int64_t ntiles(const StridedArgs& a) const { return a.nouter * a.ncolblocks; }
+  __host__ __device__ __forceinline__ int64_t ntiles(const StridedArgs& a) const { return a.nouter * a.ncolblocks; }
   template <int W>
   __device__ __forceinline__ void load(const StridedArgs& a, int64_t tile, float2* dst, uint64_t* bar) const {
     int64_t o;
@@ -80,7 +80,7 @@ struct BlockTiles {
 struct RankGroupTiles {
   CUtensorMap tin[kMaxRankGroups], tout[kMaxRankGroups];
   RankGroupGeo geo;
-  __device__ __forceinline__ int64_t ntiles(const StridedArgs&) const { return geo.first[geo.ngroups]; }
+  __host__ __device__ __forceinline__ int64_t ntiles(const StridedArgs&) const { return geo.first[geo.ngroups]; }
   __device__ __forceinline__ int place(int64_t tile, int (&c)[5]) const {
     int g = 0;
     while (g + 1 < geo.ngroups && tile >= geo.first[g + 1]) ++g;
