@@ -623,6 +623,17 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), gri
         out[mode] = a.elapsed_time(b) / steps
         if mode == "fused":
             nbytes = sum(n for _, n in p.launch_info(-1, mode) + p.launch_info(+1, mode))
+    # every launch of the fused path on its own (CUDA events around each launch)
+    wf = p.workspace("fused")
+
+    def step(mode="fused", work=wf, events=None):
+        if events is not None:
+            p.set_launch_events(events[0])
+        p.execute(-1, x, y, mode, work)
+        if events is not None:
+            p.set_launch_events(events[1])
+        p.execute(+1, y, z, mode, work)
+    kernels = per_launch_times(p, step, "fused", wf, max(3, steps // 2), barrier, torch.cuda.current_stream())
     peak, _ = _peaks()
     n = math.prod(shape)
     oshape = "x".join(str(v) for v in shape[:-1] + (shape[-1] // 2 + 1,))
@@ -632,6 +643,7 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), gri
             "fused_vs_packed_speedup": round(out["packed"] / out["fused"], 3),
             "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
+            "kernels": kernels,
             "note": "c2r overwrites its input; the forward output is reused as the inverse's input"}
 
 
