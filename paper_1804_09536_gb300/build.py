@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtfft.so")
 
-SOURCES = ["tfft_kernels.cu", "tfft_spec.cu", "tfft_spec_real.cu", "tfft_tma.cu", "tfft_noalloc.cu", "tfft_pointwise.cu", "tfft_batch.cu", "tfft_tc.cu", "tfft_tc_strided.cu", "tfft_plan.cpp", "tfft_exchange.cpp",
+SOURCES = ["tfft_kernels.cu", "tfft_spec.cu", "tfft_spec_real.cu", "tfft_tma.cu", "tfft_noalloc.cu", "tfft_pointwise.cu", "tfft_batch.cu", "tfft_tc.cu", "tfft_tc_strided.cu", "tfft_blue.cu", "tfft_plan.cpp", "tfft_exchange.cpp",
            "tfft_tmageo.cpp", "tfft_exec.cpp", "tfft_hostio.cpp", "tfft_batch_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

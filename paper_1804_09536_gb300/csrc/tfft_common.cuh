@@ -280,6 +280,7 @@ struct AxisPlan {
   int width;       // lines per CTA (contiguous) or tile width W (strided)
   int radix[MAXSTAGES];
   int blue_m;      // > 0: length without a 2/3/5 plan, done by Bluestein with this convolution length
+  int blue_spec;   // 1: that convolution length has compile-time specialised kernels (width is theirs)
 };
 
 TFFT_HD int stage_radix(uint64_t code, int s) { return (int)((code >> (5 * s)) & 31); }

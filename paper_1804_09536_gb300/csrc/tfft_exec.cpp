@@ -176,7 +176,7 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.nlines = s.nlines;
     a.ap = p->aplan[s.L];
     a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[s.L]);
-    a.lines_per_cta = a.ap.spec ? a.ap.width : std::max(1, 256 / a.ap.T);
+    a.lines_per_cta = (a.ap.spec || a.ap.blue_spec) ? a.ap.width : std::max(1, 256 / a.ap.T);
     a.sign = s.sign;
     a.scale = s.scaled ? (float)s.scale_value : 1.0f;
     a.coef = s.coef;

@@ -233,6 +233,11 @@ cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s);
 cudaError_t launch_boxcopy(const BoxArgs& a, cudaStream_t s);
 cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStream_t s);
 cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStream_t s);
+// Bluestein passes with a compile-time convolution length (tfft_blue.cu):
+// whether M has them, and their lines per CTA and strided tile width.
+bool blue_spec_plan(int M, int& lines_per_cta, int& tile_width);
+cudaError_t launch_contig_blue_spec(const ContigArgs& a, const BlueArgs& b, cudaStream_t s);
+cudaError_t launch_strided_blue_spec(const StridedArgs& a, const BlueArgs& b, cudaStream_t s);
 cudaError_t launch_twiddles(float2* tw, int L, cudaStream_t s);
 
 // Batched persistent executor (tfft_batch.cu).  One segment = the tiles of

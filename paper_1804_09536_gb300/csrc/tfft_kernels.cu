@@ -585,6 +585,7 @@ cudaError_t launch_strided(const StridedArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStream_t s) {
+  if (a.ap.blue_spec) return launch_contig_blue_spec(a, b, s);
   TFFT_ALLOW_SMEM(k_blue_contig);
   if (attr != cudaSuccess) return attr;
   const int B = a.lines_per_cta;
@@ -597,6 +598,7 @@ cudaError_t launch_contig_blue(const ContigArgs& a, const BlueArgs& b, cudaStrea
 }
 
 cudaError_t launch_strided_blue(const StridedArgs& a, const BlueArgs& b, cudaStream_t s) {
+  if (a.ap.blue_spec) return launch_strided_blue_spec(a, b, s);
   TFFT_ALLOW_SMEM(k_blue_strided);
   if (attr != cudaSuccess) return attr;
   const size_t smem = 2 * (size_t)b.M * a.W * sizeof(float2) + 2 * (size_t)b.N * sizeof(int64_t);

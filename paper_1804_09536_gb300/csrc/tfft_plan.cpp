@@ -171,7 +171,7 @@ bool make_axis_plan(int L, bool strided, AxisPlan& best) {
 }
 
 int strided_width(const AxisPlan& ap) {
-  if (ap.spec) return ap.width;
+  if (ap.spec || ap.blue_spec) return ap.width;
   int W = std::max(1, std::min(32, 512 / ap.T));
   // shared memory: L x W elements (two buffers for the generic kernel; two of
   // the convolution length for Bluestein) + row tables
@@ -251,6 +251,14 @@ bool make_bluestein(tfft_plan p, int N) {
   ap.width = std::max(1, std::min(4096 / M, 512 / apm.T));  // lines per CTA (two M-buffers each)
   AxisPlan aps = ap;
   aps.width = strided_width(aps);
+  // compile-time specialised kernels for this convolution length (their own
+  // lines per CTA and tile width; 32-bit row offsets)
+  int spec_lines = 0, spec_w = 0;
+  if (p->nelems < (int64_t(1) << 31) && blue_spec_plan(M, spec_lines, spec_w)) {
+    ap.blue_spec = aps.blue_spec = 1;
+    ap.width = spec_lines;
+    aps.width = spec_w;
+  }
   p->aplan[N] = ap;
   p->aplan_s[N] = aps;
   p->blue[N] = h;

@@ -413,5 +413,73 @@ __device__ __forceinline__ void strided_tile(const StridedArgs& a, int64_t tile,
 
 
 
+// ------------------------------------------------------------ stages only
+
+// The Stockham stages of a length-L FFT on the values a thread holds for
+// column cx of an L x W tile in shared memory (the strided passes' layout:
+// position i of the column at smem[i W + cx]): on entry v holds the first
+// stage's inputs x[jt + q T + r L / R0], on exit the outputs at positions
+// jt + q T + r L / RL (natural order, self-sorting); between stages the
+// column goes through smem.  Starts and ends without a barrier: the caller
+// orders smem use around it.
+template <int L, int E, int W, int... Rs>
+__device__ __forceinline__ void strided_stages(float2 (&v)[emax<L, E, Rs...>()], float2* smem, int cx, int jt,
+                                               const float2* __restrict__ tw) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  static_for<0, NST>([&](auto S) {
+    constexpr int s = decltype(S)::value;
+    constexpr int R = radix_at<s, Rs...>();
+    constexpr int Ns = span_at<s, Rs...>();
+    if constexpr (s > 0) {
+      constexpr int Rp = radix_at<s - 1, Rs...>();
+      constexpr int Nsp = Ns / Rp;
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+        if (bf_exists<L, E, Rp>(jt, q))
+#pragma unroll
+          for (int r = 0; r < Rp; ++r) smem[stockham_out_index(jt + q * T, Nsp, Rp, r) * W + cx] = v[q * Rp + r];
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < nbf<L, E, R>(); ++q)
+        if (bf_exists<L, E, R>(jt, q))
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = smem[(jt + q * T + r * (L / R)) * W + cx];
+    }
+    spec_stage<L, E, R, Ns>(v, jt, tw);
+  });
+}
+
+// The same for one contiguous line in its padded line slot sl (the
+// contiguous passes' layout), synchronising the line's threads.
+template <int L, int E, int... Rs>
+__device__ __forceinline__ void line_stages(float2 (&v)[emax<L, E, Rs...>()], float2* sl, int jt,
+                                            const float2* __restrict__ tw) {
+  constexpr int T = L / E, NST = sizeof...(Rs);
+  constexpr int P = pad_every<Rs...>();
+  static_for<0, NST>([&](auto S) {
+    constexpr int s = decltype(S)::value;
+    constexpr int R = radix_at<s, Rs...>();
+    constexpr int Ns = span_at<s, Rs...>();
+    if constexpr (s > 0) {
+      constexpr int Rp = radix_at<s - 1, Rs...>();
+      constexpr int Nsp = Ns / Rp;
+      line_sync<T>();
+#pragma unroll
+      for (int q = 0; q < nbf<L, E, Rp>(); ++q)
+        if (bf_exists<L, E, Rp>(jt, q))
+#pragma unroll
+          for (int r = 0; r < Rp; ++r) sl[padp<P>(stockham_out_index(jt + q * T, Nsp, Rp, r))] = v[q * Rp + r];
+      line_sync<T>();
+#pragma unroll
+      for (int q = 0; q < nbf<L, E, R>(); ++q)
+        if (bf_exists<L, E, R>(jt, q))
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[q * R + r] = sl[padp<P>(jt + q * T + r * (L / R))];
+    }
+    spec_stage<L, E, R, Ns>(v, jt, tw);
+  });
+}
+
 }  // namespace tiles
 }  // namespace tfft
