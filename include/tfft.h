@@ -160,7 +160,10 @@ int tfft_plan_bind(tfft_plan plan, void *d_state, size_t bytes, void *stream);
 /*
  * Workspace of tfft_execute() in a mode, in bytes.  TFFT_MODE_FUSED: 0 for
  * C2C (the input buffer is then overwritten) -- pass one stage buffer's worth
- * to keep the input; R2C always needs one complex stage buffer.  UNFUSED and
+ * to keep the input; R2C always needs one complex stage buffer, stored with
+ * padded rows when the gathering pass along axis d-2 runs TMA-staged over a
+ * column window (odd Hermitian half on a 2-D grid: then slightly more than a
+ * stage buffer; always allocate what this call reports).  UNFUSED and
  * PACKED: two complex stage buffers.
  */
 int tfft_plan_workspace_bytes(tfft_plan plan, int mode, int keep_input, size_t *bytes);
@@ -395,7 +398,8 @@ int tfft_batch_device_status(tfft_batch batch, int *status, int reset, void *str
  * uses its input as scratch here too and leaves it undefined.  Nothing is
  * allocated: the scratch is a static __device__ array of
  * TFFT_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
- * holds until the process exits; a plan whose stage buffer is larger is
+ * holds until the process exits; a plan whose fused workspace
+ * (tfft_plan_workspace_bytes) is larger is
  * rejected with TFFT_EWORKSPACE (message in tfft_last_error()).  The current
  * device must be the one the plan was bound on (else TFFT_EINVAL).
  *

@@ -32,6 +32,7 @@ struct DevLayout {
   int64_t Mx[MAXD];
   int64_t rs[MAXD];
   const int64_t* offset;  // nranks entries (device memory in kernels)
+  int64_t pitch;          // > 0: the innermost axis is stored `pitch` apart (a padded internal layout)
 };
 
 // Inverse of Eq. decompose: which part (coord) of N split in M holds global

@@ -84,6 +84,50 @@ Step last_axis_step(tfft_plan p, int sign) {
   return s;
 }
 
+// The gathering pass along axis d - 2 of a padded real-to-complex plan
+// (plan_padding): one TMA-staged step over the column window, then the plain
+// kernel over the remaining columns on the same buffers (marked `cont`).
+// `lin` / `lout` name the padded stage-0 layout on its side.
+void add_window_pass(tfft_plan p, std::vector<Step>& v, int axis, int lin, int lout, int sign) {
+  Step s = fft_step(p, axis, lin, lout, sign);
+  s.tma = s.tc = s.tma_groups = false;
+  s.in_shift = lin == p->pad_stage ? p->pad_lead : 0;
+  s.out_shift = lout == p->pad_stage ? p->pad_lead : 0;
+  const int64_t c0 = p->win_c0, c1 = p->win_c0 + p->win_nc;
+  auto upload = [&](const std::vector<int2>& b) {
+    return std::make_pair(image_add(p, b.data(), b.size() * sizeof(int2)), (int64_t)b.size());
+  };
+  Step w = s;
+  w.tma_win = true;
+  w.tma_E = p->win_E;
+  w.tma_W = p->win_W;
+  w.win_c0 = c0;
+  w.win_nc = p->win_nc;
+  w.ncols = p->win_nc;
+  w.tma_outer_fastest = axis == 0 && w.tma_W * sizeof(float2) >= 128;
+  if (!window_side(p, lin, axis, w.tma_W, c0, p->win_nc, s.in_shift, w.gin, w.win_min) ||
+      !window_side(p, lout, axis, w.tma_W, c0, p->win_nc, s.out_shift, w.gout, w.win_mout))
+    throw std::logic_error("column window geometry changed after planning");
+  std::vector<int2> inside, outside;
+  for (const int2& b : colblock_list(p, lin, lout, w.tma_W))
+    if (b.x >= c0 && b.x + b.y <= c1) inside.push_back(b);
+  for (const int2& b : colblock_list(p, lin, lout, s.W))
+    if (b.x + b.y <= c0 || b.x >= c1) outside.push_back(b);
+  auto cbw = upload(inside);
+  w.tma_cb_off = cbw.first;
+  w.tma_ncb = cbw.second;
+  v.push_back(w);
+  if (!outside.empty()) {
+    Step r = s;
+    r.cont = true;
+    r.ncols = p->cshape[p->d - 1] - p->win_nc;
+    auto cbr = upload(outside);
+    r.cb_off = cbr.first;
+    r.ncb = cbr.second;
+    v.push_back(r);
+  }
+}
+
 void add_exchange_steps(tfft_plan p, std::vector<Step>& out, int from, int to, int mode) {
   const ExchangeBoxes& X = p->xboxes[{from, to}];
   const std::vector<BoxList>& off = p->xbox_off[{from, to}];
@@ -101,12 +145,29 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
   const int d = p->d, g = p->g;
   std::vector<Step> v;
   if (mode == TFFT_MODE_FUSED) {
+    // a padded plan keeps its complex stage-0 buffer (internal to the fused
+    // path) in the padded layout
+    const int pad = p->pad_stage;
     if (sign == TFFT_FORWARD) {
       v.push_back(last_axis_step(p, sign));
-      for (int a = d - 2; a >= 0; --a) v.push_back(fft_step(p, a, a == d - 2 ? 0 : g, g, sign));
+      if (pad >= 0) {
+        v.back().cpitch = p->st[pad].pitch;
+        v.back().out_shift = p->pad_lead;
+      }
+      for (int a = d - 2; a >= 0; --a) {
+        if (pad >= 0 && a == d - 2) add_window_pass(p, v, a, pad, g, sign);
+        else v.push_back(fft_step(p, a, a == d - 2 ? 0 : g, g, sign));
+      }
     } else {
-      for (int a = 0; a <= d - 2; ++a) v.push_back(fft_step(p, a, g, a == d - 2 ? 0 : g, sign));
+      for (int a = 0; a <= d - 2; ++a) {
+        if (pad >= 0 && a == d - 2) add_window_pass(p, v, a, g, pad, sign);
+        else v.push_back(fft_step(p, a, g, a == d - 2 ? 0 : g, sign));
+      }
       v.push_back(last_axis_step(p, sign));
+      if (pad >= 0) {
+        v.back().cpitch = p->st[pad].pitch;
+        v.back().in_shift = p->pad_lead;
+      }
     }
   } else {
     if (sign == TFFT_FORWARD) {
@@ -130,8 +191,12 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
   if (scale_here) {
     for (int k = (int)v.size() - 1; k >= 0; --k)
       if (v[k].kind != S_BOX) {
-        v[k].scaled = true;
-        v[k].scale_value = 1.0 / (double)(p->kind == TFFT_R2C ? p->nreal : p->nelems);
+        // a pass split into steps over column ranges scales in each of them
+        for (int j = k; j >= 0; --j) {
+          v[j].scaled = true;
+          v[j].scale_value = 1.0 / (double)(p->kind == TFFT_R2C ? p->nreal : p->nelems);
+          if (!v[j].cont) break;
+        }
         break;
       }
   }
@@ -145,10 +210,15 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode) {
 void assign_buffers(std::vector<Step>& v, bool destroy_input) {
   int last_move = -1;
   for (int k = 0; k < (int)v.size(); ++k)
-    if (!v[k].inplace_ok) last_move = k;
+    if (!v[k].inplace_ok && !v[k].cont) last_move = k;
   int cur = BUF_IN;
   for (int k = 0; k < (int)v.size(); ++k) {
     Step& s = v[k];
+    if (s.cont && k > 0) {  // the rest of the previous step's columns
+      s.src = v[k - 1].src;
+      s.dst = v[k - 1].dst;
+      continue;
+    }
     s.src = cur;
     if (s.inplace_ok) {
       if (cur == BUF_IN) {
@@ -166,8 +236,8 @@ void assign_buffers(std::vector<Step>& v, bool destroy_input) {
 }
 
 int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) {
-  const float2* in = static_cast<const float2*>(bufs[s.src]);
-  float2* out = static_cast<float2*>(bufs[s.dst]);
+  const float2* in = static_cast<const float2*>(bufs[s.src]) + s.in_shift;
+  float2* out = static_cast<float2*>(bufs[s.dst]) + s.out_shift;
   cudaError_t e = cudaSuccess;
   if (s.kind == S_CONTIG) {
     ContigArgs a;
@@ -218,7 +288,19 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
     a.status = reinterpret_cast<int*>(p->d_state);
     a.wait_limit = p->wait_limit;
     bool done = false;
-    if (s.tc) {
+    if (s.tma_win) {
+      alignas(64) CUtensorMap ti, to;
+      if (!encode_window_map(s.win_min, s.tma_W, in, &ti) || !encode_window_map(s.win_mout, s.tma_W, out, &to))
+        return fail(TFFT_ECUDA, "tensor map of a column window could not be encoded");
+      StridedArgs at = a;
+      at.W = s.tma_W;
+      at.colblocks = reinterpret_cast<const int2*>(p->d_state + s.tma_cb_off);
+      at.ncolblocks = s.tma_ncb;
+      at.outer_fastest = s.tma_outer_fastest ? 1 : 0;
+      e = launch_strided_tma(at, s.tma_E, s.gin, s.gout, &ti, &to, st);
+      done = true;
+    }
+    if (!done && s.tc) {
       alignas(64) CUtensorMap ti, to;
       if (encode_stage_map(p, s.tc_gin, s.axis, s.tc_W, in, &ti) &&
           encode_stage_map(p, s.tc_gout, s.axis, s.tc_W, out, &to)) {
@@ -269,9 +351,10 @@ int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st) 
   } else if (s.kind == S_REAL) {
     RealArgs a;
     a.rin = reinterpret_cast<const float*>(bufs[s.src]);
-    a.cout = static_cast<float2*>(bufs[s.dst]);
-    a.cin = static_cast<const float2*>(bufs[s.src]);
+    a.cout = out;
+    a.cin = in;
     a.rout = static_cast<float*>(bufs[s.dst]);
+    a.cpitch = s.cpitch > 0 ? s.cpitch : (int64_t)p->rplan.L + 1;
     a.nlines = s.nlines;
     a.ap = p->rplan;
     a.tw = reinterpret_cast<const float2*>(p->d_state + p->tw_off[p->rplan.L]);
@@ -348,7 +431,8 @@ int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void*
     if (work) {
       rc = check_ptr(work, "work");
       if (rc) return rc;
-      if (work_bytes < stage) return fail(TFFT_EWORKSPACE, "fused workspace must hold one stage buffer");
+      if (work_bytes < fused_work_bytes(p))
+        return fail(TFFT_EWORKSPACE, "fused workspace smaller than tfft_plan_workspace_bytes reports");
       w0 = work;
     } else if (r2c) {
       return fail(TFFT_EWORKSPACE, "real-to-complex plans need a workspace of one complex stage buffer");
@@ -367,7 +451,7 @@ int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void*
   }
   if (work) {
     const char* a = static_cast<const char*>(work);
-    const size_t wb = (mode == TFFT_MODE_FUSED) ? stage : 2 * stage;
+    const size_t wb = (mode == TFFT_MODE_FUSED) ? fused_work_bytes(p) : 2 * stage;
     const void* ptrs[2] = {in, out};
     const size_t sizes[2] = {in_bytes, out_bytes};
     for (int k = 0; k < 2; ++k) {
@@ -445,15 +529,17 @@ int tfft_plan_launch_info(tfft_plan p, int sign, int mode, int index, char* name
       elems = s.box_elems;
     } else {
       const AxisPlan& ap = (s.kind == S_CONTIG) ? p->aplan[s.L] : p->aplan_s[s.L];
-      const bool tma = s.kind == S_STRIDED && (s.tma || s.tc || s.tma_groups);
+      const bool tma = s.kind == S_STRIDED && (s.tma || s.tc || s.tma_groups || s.tma_win);
       const bool tc = p->precision != TFFT_FP32 && ((s.kind == S_CONTIG && tc_supported(ap.L)) || s.tc);
       nm = std::string(s.kind == S_CONTIG ? "fft_contig" : "fft_strided") +
            (tma ? "_tma" : "") + (s.kind == S_STRIDED && s.tma_groups && !s.tc ? "_groups" : "") +
+           (s.kind == S_STRIDED && s.tma_win ? "_window" : "") +
            (tc ? (p->precision == TFFT_TC_BF16X3 ? "_tc_bf16x3" : "_tc_fp16x3") : "") +
            (ap.blue_m ? "_bluestein_L" + std::to_string(ap.L)
                       : ap.spec ? "_L" + std::to_string(ap.L)
                                 : ap.E == 0 ? std::string("_generic") : "_E" + std::to_string(ap.E));
       elems = p->nelems;
+      if (s.ncols >= 0) elems = p->nelems / p->cshape[p->d - 1] * s.ncols;  // a column range of the pass
     }
     *bytes = 2 * elems * (int64_t)sizeof(float2);  // one read and one write of every element
     if (name_len > 0) {

@@ -6,7 +6,7 @@ namespace {
 
 constexpr int kHostSetBufs = 4;  // per buffer set: input, intermediate, output, workspace
 
-size_t host_buf_bytes(tfft_plan p) { return align_up((size_t)p->nelems * sizeof(float2), 256); }
+size_t host_buf_bytes(tfft_plan p) { return align_up(fused_work_bytes(p), 256); }
 
 int ensure_host_io(tfft_plan p) {
   int dev = 0;

@@ -56,13 +56,14 @@ __device__ __forceinline__ float contig_scale(const ContigArgs& a) {
 // computed with one complex FFT of length L per line.
 struct RealArgs {
   const float* rin;     // r2c input (nlines x 2L floats)
-  float2* cout;         // r2c output (nlines x (L + 1))
+  float2* cout;         // r2c output (nlines x cpitch, the first L + 1 of each written)
   const float2* cin;    // c2r input
   float* rout;          // c2r output
   int64_t nlines;
   AxisPlan ap;          // plan of the length-L complex FFT
   const float2* tw;     // L roots exp(-2 pi i m / L)
   const float2* tw2;    // 2L roots exp(-2 pi i m / 2L)
+  int64_t cpitch;       // complex elements from one line's start to the next (>= L + 1)
   int dir;
   float scale;
   int* status;
@@ -144,6 +145,7 @@ struct TileRows {
         locate(lay.N[m], lay.Mx[m], g, c, local, n);
         base += c * lay.rs[m];
       }
+      if (m == lay.d - 1 && lay.pitch > 0) n = lay.pitch;  // the innermost axis' storage extent
       if (m < a.axis) {
         head = head * n + local;
       } else {
@@ -179,6 +181,9 @@ struct TmaGeo {
   // axis m; split = 0 for the plain view
   int split;
   int rmul[3];
+  // first column of the view: a tile's column c is at c - c0 of the tensor
+  // map (a view over a window of the innermost axis; 0 for a whole stage)
+  int c0;
 };
 
 // Rank groups of an uneven stage layout seen by the TMA passes along its

@@ -34,7 +34,7 @@ size_t image_add(tfft_plan p, const void* data, size_t bytes) {
   return off;
 }
 
-void build_layout(tfft_plan p, const int64_t* shape, int stage, LayoutH& L) {
+void build_layout(tfft_plan p, const int64_t* shape, int stage, LayoutH& L, int64_t pitch) {
   L.d = p->d;
   for (int m = 0; m < MAXD; ++m) {
     L.N[m] = m < p->d ? shape[m] : 1;
@@ -62,12 +62,13 @@ void build_layout(tfft_plan p, const int64_t* shape, int stage, LayoutH& L) {
       if (L.owner[m] >= 0) decompose(L.N[m], p->grid[L.owner[m]], coords[L.owner[m]], n, s);
       L.start[(size_t)r * p->d + m] = s;
       L.size[(size_t)r * p->d + m] = n;
-      cnt *= n;
+      cnt *= (m == p->d - 1 && pitch > 0) ? pitch : n;
     }
     L.offset[r] = off;
     off += cnt;
   }
   L.total = off;
+  L.pitch = pitch;
 }
 
 DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
@@ -79,6 +80,7 @@ DevLayout dev_layout(tfft_plan p, const LayoutH& L) {
     D.rs[m] = L.owner[m] >= 0 ? p->rstride[L.owner[m]] : 0;
   }
   D.offset = reinterpret_cast<const int64_t*>(p->d_state + L.state_off);
+  D.pitch = L.pitch;
   return D;
 }
 
@@ -416,6 +418,8 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
       build_exchange(p, s, s - 1);
     }
     if (p->transformable) {
+      // padded stage-0 layout of a real-to-complex plan's fused path
+      plan_padding(p);
       // pass lists
       for (int sign : {TFFT_FORWARD, TFFT_BACKWARD})
         for (int mode : {TFFT_MODE_FUSED, TFFT_MODE_UNFUSED, TFFT_MODE_PACKED})
@@ -530,7 +534,7 @@ int tfft_plan_workspace_bytes(tfft_plan p, int mode, int keep_input, size_t* byt
   if (!p || !bytes) return fail(TFFT_EINVAL, "NULL argument");
   const size_t stage = (size_t)p->nelems * sizeof(float2);
   switch (mode) {
-    case TFFT_MODE_FUSED: *bytes = (keep_input || p->kind == TFFT_R2C) ? stage : 0; break;
+    case TFFT_MODE_FUSED: *bytes = (keep_input || p->kind == TFFT_R2C) ? fused_work_bytes(p) : 0; break;
     case TFFT_MODE_UNFUSED:
     case TFFT_MODE_PACKED: *bytes = 2 * stage; break;
     default: return fail(TFFT_EINVAL, "unknown mode");

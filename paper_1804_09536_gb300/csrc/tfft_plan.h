@@ -48,6 +48,9 @@ struct LayoutH {
   std::vector<int64_t> start, size, offset;  // nranks * d, nranks * d, nranks
   int64_t total = 0;
   size_t state_off = 0;  // rank offset table in the state image (bytes)
+  // > 0: every rank's innermost axis is stored `pitch` elements apart (a
+  // padded internal copy of a stage; the public stage buffers have none)
+  int64_t pitch = 0;
 };
 
 enum StepKind { S_CONTIG, S_STRIDED, S_BOX, S_REAL };
@@ -61,6 +64,15 @@ enum BufId { BUF_IN, BUF_OUT, BUF_W0, BUF_W1 };
 struct RankGroupH {
   int64_t base = 0, inner = 0, s1 = 0, s0 = 0;
   int ext1 = 1, ext0 = 1;
+};
+
+// A tensor map described on the host: base element offset inside its buffer,
+// extents and byte strides of the 5-D view, and the box of one copy.
+struct TmaMapH {
+  int64_t base = 0;
+  uint64_t dims[5] = {1, 1, 1, 1, 1};
+  uint64_t strides[4] = {0, 0, 0, 0};
+  uint32_t box[5] = {1, 1, 1, 1, 1};
 };
 
 struct Step {
@@ -100,6 +112,20 @@ struct Step {
   bool tma_groups = false;
   RankGroupGeo rg{};
   std::vector<RankGroupH> rgh;
+  // TMA pass over one column window [win_c0, win_c0 + win_nc) of the
+  // innermost axis (the columns whose ranks are TMA-describable on both
+  // sides); the other columns run as the next step, which is marked `cont`
+  bool tma_win = false;
+  int64_t win_c0 = 0, win_nc = 0;
+  TmaMapH win_min{}, win_mout{};
+  // this step runs on the previous step's buffers (the rest of its columns)
+  bool cont = false;
+  int64_t ncols = -1;  // columns of the innermost axis the step covers (-1: all)
+  // element shifts of the input / output pointers (a padded internal buffer
+  // starts its rows `pad_lead` elements in) and the complex row pitch of a
+  // real pass (0: L + 1)
+  int64_t in_shift = 0, out_shift = 0;
+  int64_t cpitch = 0;
 };
 
 struct ExchangeBoxes {  // one adjacent-stage exchange
@@ -136,6 +162,14 @@ struct tfft_plan_s {
   bool transformable = true;  // every axis length has an FFT plan
   bool use_tma = true;        // TMA-staged passes where their conditions hold
   size_t red_off = 0;         // reduction scratch in the state (kReductionParts doubles)
+  // real-to-complex plans whose gathering pass along axis d - 2 runs
+  // TMA-staged over a column window: the complex stage-0 buffer of the fused
+  // path (internal) is stored with rows `pitch` elements apart, starting
+  // `pad_lead` elements in, as layout st[pad_stage]; -1 when not padded
+  int pad_stage = -1;
+  int64_t pad_lead = 0;
+  int64_t win_c0 = 0, win_nc = 0;  // the TMA column window of that pass
+  int win_E = 0, win_W = 0;        // its TMA variant
   uint32_t wait_limit = 1u << 22;  // polls of a bounded copy wait
   std::vector<LayoutH> st;
   std::map<int, AxisPlan> aplan;   // contiguous-line passes
@@ -181,7 +215,7 @@ namespace host {
 
 // ---- plan state image, layouts, per-length plans (tfft_plan.cpp)
 size_t image_add(tfft_plan p, const void* data, size_t bytes);
-void build_layout(tfft_plan p, const int64_t* shape, int stage, LayoutH& L);
+void build_layout(tfft_plan p, const int64_t* shape, int stage, LayoutH& L, int64_t pitch = 0);
 DevLayout dev_layout(tfft_plan p, const LayoutH& L);
 bool make_axis_plan(int L, bool strided, AxisPlan& best);
 int strided_width(const AxisPlan& ap);
@@ -207,6 +241,11 @@ bool encode_stage_map(tfft_plan p, const TmaGeo& G, int axis, int W, const void*
 int tuned_width(int L, int* E = nullptr, const char* var = "TFFT_TMA_W");
 bool rank_groups(tfft_plan p, int stage, int L, int W, RankGroupGeo& G, std::vector<RankGroupH>& groups);
 bool encode_group_map(const RankGroupH& H, int L, int W, const void* base, CUtensorMap* map);
+bool window_side(tfft_plan p, int stage, int axis, int W, int64_t c0, int64_t nc, int64_t shift, TmaGeo& G,
+                 TmaMapH& D);
+bool encode_window_map(const TmaMapH& D, int W, const void* base, CUtensorMap* map);
+bool plan_padding(tfft_plan p);
+size_t fused_work_bytes(tfft_plan p);
 
 // ---- pass lists and launches (tfft_exec.cpp)
 Step fft_step(tfft_plan p, int axis, int lin, int lout, int sign);

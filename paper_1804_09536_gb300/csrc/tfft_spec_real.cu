@@ -35,7 +35,7 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
     const int64_t line = base + ly;
     const bool act = line < a.nlines;
     const float2* src = reinterpret_cast<const float2*>(a.rin) + line * L;
-    float2* dst = a.cout + line * (L + 1);
+    float2* dst = a.cout + line * a.cpitch;
     const int jt = opaque_tid_x();
     float2 v[emax<L, E, Rs...>()];
     static_for<0, NST>([&](auto S) {
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
   for (int64_t base = (int64_t)blockIdx.x * B; base < a.nlines; base += (int64_t)gridDim.x * B) {
     const int64_t line = base + ly;
     const bool act = line < a.nlines;
-    const float2* src = a.cin + line * (L + 1);
+    const float2* src = a.cin + line * a.cpitch;
     float2* dst = reinterpret_cast<float2*>(a.rout) + line * L;
     const int jt = opaque_tid_x();
     // the L + 1 inputs: every load issued before the first shared store, so

@@ -54,7 +54,7 @@ struct BlockTiles {
     const int tax = (a.oax0 >= 0) ? a.oax0 : -1;  // the outer axis (d == 3)
     for (int k = 0; k < gin.nops; ++k) {
       int c[5];
-      tile_coords(gin, a.axis, k, blk.x, o, tax, c);
+      tile_coords(gin, a.axis, k, (int64_t)blk.x - gin.c0, o, tax, c);
       tma_load_5d(dst + (size_t)k * gin.rows_per_op * W, &tin, bar, c);
     }
   }
@@ -66,7 +66,7 @@ struct BlockTiles {
     const int tax = (a.oax0 >= 0) ? a.oax0 : -1;
     for (int k = 0; k < gout.nops; ++k) {
       int c[5];
-      tile_coords(gout, a.axis, k, blk.x, o, tax, c);
+      tile_coords(gout, a.axis, k, (int64_t)blk.x - gout.c0, o, tax, c);
       tma_store_5d(&tout, src + (size_t)k * gout.rows_per_op * W, c);
     }
   }

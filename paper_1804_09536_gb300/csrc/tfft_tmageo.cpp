@@ -20,7 +20,9 @@ int split_rows(int L) {
 bool tma_geo(tfft_plan p, int stage, int axis, int W, TmaGeo& G) {
   if (p->d != 3 || p->g < 1 || p->g > 2) return false;
   const LayoutH& S = p->st[stage];
+  if (S.pitch > 0) return false;  // padded rows: window_side describes those
   const int L = (int)p->cshape[axis];
+  G.c0 = 0;
   for (int m = 0; m < 3; ++m) {
     G.cut[m] = S.owner[m] >= 0 ? 1 : 0;
     const int64_t M = G.cut[m] ? p->grid[S.owner[m]] : 1;
@@ -220,6 +222,205 @@ bool encode_group_map(const RankGroupH& H, int L, int W, const void* base, CUten
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<char*>(b), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// One side (a stage layout) of a TMA pass along `axis` over the column window
+// [c0, c0 + nc) of the innermost axis (d == 3 on a 2-D grid): the 5-D view
+// [x][n1][n0][ranks of direction 1][ranks of direction 0] of the ranks that
+// hold the window, with the box of one tile (W columns x every row of the
+// line: the local rows of all ranks of the subgroup that cuts `axis`).  When
+// the layout cuts the innermost axis, the window must be tiled exactly by
+// ranks of one width (a multiple of W) whose offsets are affine in their grid
+// coordinates; when it does not, the window lies inside every row (rows
+// `pitch` apart in a padded layout).  `shift` is the element offset of the
+// layout's origin in its buffer.  Every stride and the base must be 16-byte
+// aligned, and the view must stay inside the layout's elements: this is
+// checked here, before any map is made.
+bool window_side(tfft_plan p, int stage, int axis, int W, int64_t c0, int64_t nc, int64_t shift, TmaGeo& G,
+                 TmaMapH& D) {
+  if (p->d != 3 || p->g != 2 || axis < 0 || axis > 1 || W < 2 || (W & 1) || nc < W) return false;
+  if (stage < 0 || stage >= (int)p->st.size()) return false;
+  const LayoutH& S = p->st[stage];
+  if (S.owner[axis] < 0) return false;  // the box spans the ranks that cut the FFT axis
+  G = TmaGeo{};
+  G.split = 0;
+  G.nops = 1;
+  G.rows_per_op = (int)p->cshape[axis];
+  G.c0 = (int)c0;
+  int lo[2] = {0, 0}, cnt[2] = {p->grid[0], p->grid[1]};
+  for (int m = 0; m < 3; ++m) {
+    G.cut[m] = S.owner[m] >= 0 ? 1 : 0;
+    G.rdim[m] = G.cut[m] ? 3 + (p->g - 1 - S.owner[m]) : 0;
+    if (!G.cut[m]) {
+      G.n[m] = (int)(m == 2 ? nc : p->cshape[m]);
+      continue;
+    }
+    const int k = S.owner[m];
+    const int M = p->grid[k];
+    if (m == 2) {
+      // the ranks of direction k whose columns tile the window
+      int first = -1;
+      for (int c = 0; c < M; ++c) {
+        int64_t n = 0, s0 = 0;
+        decompose(p->cshape[2], M, c, n, s0);
+        if (s0 == c0 && n > 0) first = c;
+      }
+      if (first < 0) return false;
+      int64_t q = 0, s0 = 0;
+      decompose(p->cshape[2], M, first, q, s0);
+      if (nc % q || q % W) return false;
+      const int64_t ranks = nc / q;
+      for (int64_t j = 0; j < ranks; ++j) {
+        int64_t n = 0, s1 = 0;
+        if (first + j >= M) return false;
+        decompose(p->cshape[2], M, (int)(first + j), n, s1);
+        if (n != q || s1 != c0 + j * q) return false;
+      }
+      G.n[2] = (int)q;
+      lo[k] = first;
+      cnt[k] = (int)ranks;
+    } else {
+      if (p->cshape[m] % M) return false;
+      G.n[m] = (int)(p->cshape[m] / M);
+    }
+  }
+  const int ka = S.owner[axis];
+  if (G.n[axis] > 256 || p->grid[ka] > 256 || lo[ka] != 0 || cnt[ka] != p->grid[ka]) return false;
+  // the window's ranks: equal local blocks, offsets affine in (c0, c1)
+  auto rank_at = [&](int i0, int i1) { return (int)((lo[0] + i0) * p->rstride[0] + (lo[1] + i1) * p->rstride[1]); };
+  const int r00 = rank_at(0, 0);
+  const int64_t rowlen = S.pitch > 0 ? S.pitch : (G.cut[2] ? G.n[2] : p->cshape[2]);
+  const int64_t block = (int64_t)G.n[0] * G.n[1] * rowlen;
+  const int64_t sd[2] = {cnt[0] > 1 ? S.offset[rank_at(1, 0)] - S.offset[r00] : block,
+                         cnt[1] > 1 ? S.offset[rank_at(0, 1)] - S.offset[r00] : block};
+  for (int i0 = 0; i0 < cnt[0]; ++i0)
+    for (int i1 = 0; i1 < cnt[1]; ++i1) {
+      const int r = rank_at(i0, i1);
+      for (int m = 0; m < 3; ++m) {
+        const int64_t want = (m == 2 && !G.cut[2]) ? p->cshape[2] : G.n[m];
+        if (S.size[(size_t)r * 3 + m] != want) return false;
+      }
+      if (S.offset[r] != S.offset[r00] + i0 * sd[0] + i1 * sd[1]) return false;
+    }
+  if (!G.cut[2] && c0 + nc > p->cshape[2]) return false;
+  D = TmaMapH{};
+  D.base = S.offset[r00] + (G.cut[2] ? 0 : c0);
+  D.dims[0] = (uint64_t)(G.cut[2] ? G.n[2] : nc);
+  D.dims[1] = (uint64_t)G.n[1];
+  D.dims[2] = (uint64_t)G.n[0];
+  D.dims[3] = (uint64_t)cnt[1];  // direction g - 1 = 1
+  D.dims[4] = (uint64_t)cnt[0];  // direction 0
+  D.strides[0] = (uint64_t)rowlen * 8;
+  D.strides[1] = (uint64_t)(G.n[1] * rowlen) * 8;
+  D.strides[2] = (uint64_t)sd[1] * 8;
+  D.strides[3] = (uint64_t)sd[0] * 8;
+  D.box[0] = (uint32_t)W;
+  D.box[2 - axis] = (uint32_t)G.n[axis];
+  D.box[G.rdim[axis]] = (uint32_t)p->grid[ka];
+  // 16-byte alignment of the base and every stride
+  if ((shift + D.base) & 1) return false;
+  for (int i = 0; i < 4; ++i)
+    if ((D.strides[i] % 16) || D.strides[i] == 0) return false;
+  // the farthest element the view can address stays inside the layout's
+  // buffer (S.total elements from the buffer's start)
+  int64_t last = D.base + (int64_t)D.dims[0] - 1;
+  for (int i = 0; i < 4; ++i) last += (int64_t)(D.dims[i + 1] - 1) * (int64_t)(D.strides[i] / 8);
+  if (D.base < 0 || shift < 0 || shift + last >= S.total) return false;
+  return true;
+}
+
+bool encode_window_map(const TmaMapH& D, int W, const void* base, CUtensorMap* map) {
+  auto enc = tensor_map_encoder();
+  if (!enc || (int)D.box[0] != W) return false;
+  const char* b = static_cast<const char*>(base) + D.base * 8;
+  cuuint64_t dims[5];
+  cuuint64_t strides[4];
+  cuuint32_t box[5];
+  for (int i = 0; i < 5; ++i) {
+    dims[i] = (cuuint64_t)D.dims[i];
+    box[i] = (cuuint32_t)D.box[i];
+  }
+  for (int i = 0; i < 4; ++i) strides[i] = (cuuint64_t)D.strides[i];
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapL2promotion promo =
+      W * 8 >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, const_cast<char*>(b), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Padding of the internal complex stage-0 buffer of a real-to-complex plan
+// (d == 3, 2-D grid, FP32): when the gathering pass along axis 1 cannot run
+// TMA-staged on the plain layouts -- the Hermitian half N2 = n/2 + 1 is odd,
+// so stage-0 rows are not 16-byte multiples and the last stage's split of
+// N2 is uneven -- the stage-0 rows are padded to an even pitch with a lead
+// that puts the first column of the TMA-describable rank class on a 16-byte
+// boundary.  That class (the ranks of one width, a multiple of the tile
+// width) then runs TMA-staged; the other class runs the plain kernel.
+bool plan_padding(tfft_plan p) {
+  if (p->kind != TFFT_R2C || p->d != 3 || p->g != 2 || !p->use_tma || p->precision != TFFT_FP32) return false;
+  const int ax = p->d - 2;
+  const int L = (int)p->cshape[ax];
+  auto it = p->aplan_s.find(L);
+  if (it == p->aplan_s.end() || !it->second.spec) return false;
+  int wantE = 0, Et = 0, Wt = 0;
+  const int wantW = tuned_width(L, &wantE);
+  if (!tma_strided_variant(L, wantW, wantE, Et, Wt)) return false;
+  TmaGeo a{}, b{};
+  if (tma_geo(p, 0, ax, Wt, a) && tma_geo(p, p->g, ax, Wt, b)) return false;  // no padding needed
+  const LayoutH& S = p->st[p->g];
+  const int k2 = S.owner[2];
+  if (k2 < 0) return false;
+  const int64_t N2 = p->cshape[2], M = p->grid[k2], q = N2 / M, r = N2 % M;
+  // candidate classes: the r ranks of width q + 1, the M - r ranks of width q
+  int64_t c0 = -1, nc = 0;
+  if (r > 0 && (q + 1) % Wt == 0 && r * (q + 1) > nc) {
+    c0 = 0;
+    nc = r * (q + 1);
+  }
+  if (M - r > 0 && q > 0 && q % Wt == 0 && (M - r) * q > nc) {
+    c0 = r * (q + 1);
+    nc = (M - r) * q;
+  }
+  if (c0 < 0) return false;
+  // the window's first column on a 128-byte line (16 complex): every tile row
+  // of the padded side is then whole lines (measured on 512^3, 4 x 8: with
+  // 16-byte alignment only, rows straddled two lines and the window pass ran
+  // at 0.85 of HBM); 16-byte alignment when 128 would cost over 1/16 more
+  // memory
+  int64_t lead = (16 - c0 % 16) % 16;
+  int64_t pitch = (lead + N2 + 15) / 16 * 16;
+  if (16 * (pitch - N2) > N2) {
+    lead = c0 & 1;
+    pitch = (lead + N2 + 1) & ~int64_t(1);
+  }
+  LayoutH P;
+  build_layout(p, p->cshape, 0, P, pitch);
+  if (P.total >= (int64_t(1) << 31)) return false;  // 32-bit row offsets of the plain kernel
+  p->st.push_back(P);
+  const int idx = (int)p->st.size() - 1;
+  TmaGeo gi{}, go{};
+  TmaMapH mi{}, mo{};
+  if (!window_side(p, idx, ax, Wt, c0, nc, lead, gi, mi) || !window_side(p, p->g, ax, Wt, c0, nc, 0, go, mo)) {
+    p->st.pop_back();
+    return false;
+  }
+  p->st[idx].state_off = image_add(p, p->st[idx].offset.data(), p->st[idx].offset.size() * 8);
+  p->pad_stage = idx;
+  p->pad_lead = lead;
+  p->win_c0 = c0;
+  p->win_nc = nc;
+  p->win_E = Et;
+  p->win_W = Wt;
+  return true;
+}
+
+// Workspace of the fused path: one stage buffer, or the padded stage-0
+// buffer of a real-to-complex plan when that is larger.
+size_t fused_work_bytes(tfft_plan p) {
+  size_t b = (size_t)p->nelems * sizeof(float2);
+  if (p->pad_stage >= 0) b = std::max(b, (size_t)p->st[p->pad_stage].total * sizeof(float2));
+  return b;
 }
 
 }  // namespace host

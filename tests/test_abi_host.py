@@ -145,3 +145,45 @@ def test_batch_issue_order(lib, which):
     order, npass = _batch_order(lib, problems)
     want = [(t, k) for k in range(max(npass)) for t in range(len(problems)) if k < npass[t]]
     assert order == want
+
+
+@pytest.mark.parametrize("shape,grid,c0,nc", [((512, 512, 512), (4, 8), 33, 224),
+                                               ((64, 128, 512), (4, 8), 33, 224),
+                                               ((128, 64, 256), (2, 4), 33, 96),
+                                               ((16, 512, 120), (2, 4), 0, 16)])
+def test_r2c_column_window_plan(lib, shape, grid, c0, nc):
+    """Real-to-complex plans with odd stage-0 rows: the fused gathering pass
+    along axis 1 is one TMA step over the column window plus the plain kernel
+    over the other columns; their algorithmic bytes add up to one whole pass,
+    and the fused workspace is the padded stage-0 buffer (rows of an even
+    pitch, the window's first column on a 16-byte boundary).  Unfused, packed
+    and no-TMA plans keep the plain layouts."""
+    from paper_1804_09536_gb300.plan import Plan
+    p = Plan(shape, grid, kind="r2c", bind=False)
+    n2 = shape[-1] // 2 + 1
+    rows = math.prod(shape[:-1])
+    # rows padded so that the window's first column starts a 128-byte line,
+    # unless that costs over 1/16 more memory (then a 16-byte boundary)
+    lead = (16 - c0 % 16) % 16
+    pitch = (lead + n2 + 15) // 16 * 16
+    if 16 * (pitch - n2) > n2:
+        lead = c0 % 2
+        pitch = (lead + n2 + 1) // 2 * 2
+    assert (lead + c0) * 8 % 16 == 0 and pitch * 8 % 16 == 0
+    assert p.workspace_bytes("fused") == 8 * rows * pitch
+    assert p.workspace_bytes("unfused") == 2 * 8 * rows * n2
+    whole = 2 * 8 * rows * n2
+    for sign in (-1, 1):
+        info = p.launch_info(sign)
+        win = [b for n, b in info if "tma_window" in n]
+        rest = [b for n, b in info if n.startswith("fft_strided_L")]
+        assert len(win) == 1 and len(rest) == 1, info
+        assert win[0] == 2 * 8 * rows * nc
+        assert win[0] + rest[0] == whole
+        assert p.num_launches(sign, "fused") == len(info) == 4
+        assert not any("window" in n for n, _ in p.launch_info(sign, "unfused"))
+    q = Plan(shape, grid, kind="r2c", bind=False, tma=False)
+    assert q.workspace_bytes("fused") == 8 * rows * n2
+    assert not any("window" in n for n, _ in q.launch_info(-1))
+    c = Plan(shape, grid, kind="r2c", bind=False, precision="bf16x3")
+    assert not any("window" in n for n, _ in c.launch_info(-1))

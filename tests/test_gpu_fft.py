@@ -277,6 +277,51 @@ def test_full_size_128_4d_sampled(cuda_device):
     assert float(diff) <= RTOL_FP32
 
 
+@pytest.mark.parametrize("shape,grid", [((64, 128, 512), (4, 8)),    # 257 = 33 + 7 x 32: window over ranks 1..7, lead 1
+                                         ((128, 64, 256), (2, 4)),    # 129 = 33 + 3 x 32
+                                         ((32, 512, 512), (4, 8)),    # the pencil workload's axis-1 length
+                                         ((16, 512, 120), (2, 4)),    # 61 = 16 + 3 x 15: window over rank 0, no lead
+                                         ((8, 160, 120), (2, 4))])    # a 5-smooth length, window over rank 0
+def test_r2c_column_window_passes(cuda_device, shape, grid):
+    """Real-to-complex plans whose stage-0 rows are odd: the fused path keeps its
+    complex stage-0 buffer with padded rows and runs the gathering pass along
+    axis 1 TMA-staged over the column window of the ranks of one even width,
+    the other columns with the plain kernel.  Forward and inverse against the
+    oracle and against the plan without TMA passes (same bits where the two
+    kernels use the same radices)."""
+    from paper_1804_09536_gb300.plan import Plan
+    pt = Plan(shape, grid, kind="r2c", device=cuda_device)
+    pp = Plan(shape, grid, kind="r2c", device=cuda_device, tma=False)
+    for sign in (-1, +1):
+        names = [n for n, _ in pt.launch_info(sign)]
+        assert sum("tma_window" in n for n in names) == 1, names
+    assert pt.workspace_bytes("fused") > pp.workspace_bytes("fused")
+    x = inputs.normal_real(shape, seed=21).numpy()
+    b0 = R.scatter(x, grid, 0)
+    want = dft.distributed_rfft_forward(b0.astype(np.float64), shape, grid)
+    xin = to_dev(b0, cuda_device)
+    yt = pt.forward(xin)
+    yp = pp.forward(to_dev(b0, cuda_device))
+    zt = pt.inverse(yt.clone())
+    zp = pp.inverse(yp.clone())
+    torch.cuda.synchronize()
+    assert pt.device_status() == 0
+    assert np.array_equal(bits(xin), b0.view(np.uint8)), "r2c keeps its input"
+    assert rel_l2(yt.cpu().numpy(), want) <= RTOL_FP32
+    want_b = dft.distributed_irfft_backward(want, shape, grid)
+    assert rel_l2(zt.cpu().numpy(), want_b) <= RTOL_FP32
+    if shape[1] != 512:
+        assert np.array_equal(bits(yt), bits(yp))
+        assert np.array_equal(bits(zt), bits(zp))
+    else:
+        assert rel_l2(yt.cpu().numpy(), yp.cpu().numpy()) <= 2e-6
+        assert rel_l2(zt.cpu().numpy(), zp.cpu().numpy()) <= 2e-6
+    # unfused and packed paths (plain layouts) give the same transform
+    yu = pt.forward(to_dev(b0, cuda_device), mode="unfused")
+    torch.cuda.synchronize()
+    assert rel_l2(yu.cpu().numpy(), want) <= RTOL_FP32
+
+
 R2C_CASES = [
     ((8, 12, 480), (2, 2)),          # half-length 240 (2.3.5)
     ((4, 8, 2048), (2, 2)),          # half-length 1024
