@@ -820,8 +820,10 @@ def autograd_step(plan, x, dev, steps, barrier):
 
 
 def batch48(dev, steps, barrier, autotune=True):
-    """48 transforms drawn from the uneven-shape set: one persistent launch per
-    forward, replayed from a CUDA graph, vs the same transforms launched plan by plan."""
+    """48 transforms drawn from the uneven-shape set: the autotuned batch executor
+    (one persistent launch, or the plans' own kernels on forked streams) replayed
+    from a CUDA graph, vs the same transforms launched plan by plan, eagerly and
+    from one CUDA graph."""
     import torch
     from paper_1804_09536_gb300 import inputs
     from paper_1804_09536_gb300.plan import Batch, Plan
@@ -835,6 +837,7 @@ def batch48(dev, steps, barrier, autotune=True):
         b.autotune(reps=3)
         for t, k in zip(b.ins, x_keep):
             t.copy_(k)
+    chosen = b.executor
     g = b.graph()
 
     def timed(fn):
@@ -850,12 +853,30 @@ def batch48(dev, steps, barrier, autotune=True):
         barrier()
         return a.elapsed_time(e) / steps
     ms_graph = timed(g.replay)
+    # both executors, each replayed from its own graph
+    execs = {}
+    for kind, n in (("persistent", 0), ("streams", chosen[1] if chosen[0] == "streams" else 4)):
+        b.set_executor(kind, max(1, n))
+        execs[kind if kind == "persistent" else f"streams{n}"] = round(timed(b.graph().replay), 4)
+    b.set_executor(chosen[0], max(1, chosen[1]))
     works = [p.workspace("fused", True) for p in plans]
 
     def per_plan():
         for k, p in enumerate(plans):
             p.execute(-1, b.ins[k], b.outs[k], "fused", works[k])
     ms_plans = timed(per_plan)
+    # the per-plan loop captured in one CUDA graph (one stream): the baseline
+    # without host launch cost
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        per_plan()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp):
+        per_plan()
+    ms_plans_graph = timed(gp.replay)
     nsum = sum(math.prod(sh) for sh, _ in problems)
     flops = sum(5.0 * math.prod(sh) * math.log2(math.prod(sh)) for sh, _ in problems)
     nbytes = 3 * 16 * nsum
@@ -864,8 +885,11 @@ def batch48(dev, steps, barrier, autotune=True):
     return {"workload": "48 c2c complex64 transforms, shapes drawn (seed 0) from {64^3, 96^3, 128^3, "
                         "64x128x256, 160^3, 256^3}, grids from {1x2, 2x2, 2x4}; forward",
             "elements": nsum, "items": items, "segments": segs,
-            "graph_ms": round(ms_graph, 4), "per_plan_ms": round(ms_plans, 4),
+            "executor": {"kind": chosen[0], "streams": chosen[1]},
+            "graph_ms": round(ms_graph, 4), "executor_graph_ms": execs,
+            "per_plan_ms": round(ms_plans, 4), "per_plan_graph_ms": round(ms_plans_graph, 4),
             "speedup_vs_per_plan": round(ms_plans / ms_graph, 3),
+            "speedup_vs_per_plan_graph": round(ms_plans_graph / ms_graph, 3),
             "GFLOPs": round(flops / (ms_graph * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (ms_graph * 1e-3) / 1e9 / peak, 4),
             "autotuned": bool(autotune),

@@ -347,14 +347,20 @@ int tfft_plan_set_launch_events(tfft_plan plan, void *const *events, int count);
  *                       (work[t] may be NULL: input t is then scratch)
  *   tfft_batch_execute  one memset of the queue counters + one kernel launch,
  *                       stream-ordered, no allocation and no host sync (so a
- *                       CUDA graph can capture it)
+ *                       CUDA graph can capture it) -- or, with the stream
+ *                       executor (tfft_batch_set_executor), every transform's
+ *                       own pass kernels on forked streams, joined back
  *   tfft_batch_autotune picks, per pass kind and length, the fastest of the
  *                       compiled tile variants (elements per thread, tile
  *                       width / lines per group) by timing the whole batch
  *                       (`reps` runs per candidate); it runs the batch on the
  *                       bound buffers (their contents are overwritten) and
  *                       synchronises.  With TFFT_AUTOTUNE_CACHE set, choices
- *                       are read from / written to that file.
+ *                       are read from / written to that file.  Then it
+ *                       times the persistent kernel against the stream
+ *                       executor with 1, 2, 3, 4, 6 and 8 streams and keeps
+ *                       the fastest executor (cached as the line "-1 -1 K",
+ *                       K = streams, 0 = persistent).
  * The paper has no batched executor; each transform follows its plan's steps.
  */
 typedef struct tfft_batch_s *tfft_batch;
@@ -382,8 +388,30 @@ int tfft_batch_set_variant(tfft_batch batch, int kind, int L, int variant, void 
 /* Clock cycles a batch tile may wait for the previous pass (0: default ~2 s);
    a tiny value makes the waits expire on purpose (error-path tests). */
 int tfft_batch_set_wait_limit(tfft_batch batch, long long cycles);
-/* Status word of the batch state (as tfft_plan_device_status). */
+/* Status of the batch: the OR of its state's status word and its plans'
+   (the stream executor's kernels report in their plans' states); `reset`
+   clears all of them.  As tfft_plan_device_status otherwise. */
 int tfft_batch_device_status(tfft_batch batch, int *status, int reset, void *stream);
+
+/* Executors of tfft_batch_execute. */
+enum {
+  TFFT_BATCH_PERSISTENT = 0, /* one persistent kernel over every pass (the default) */
+  TFFT_BATCH_STREAMS = 1     /* each transform's own pass kernels, on forked streams */
+};
+/* Choose the executor (host only; no GPU work).  TFFT_BATCH_STREAMS: the
+   transforms are dealt, longest first, to the least-loaded of `nstreams`
+   (1..16, at most the transform count) streams; on execute, an event on the
+   caller's stream forks them, each runs its transforms' fused passes one after
+   the other with the standalone kernels of their plans (so independent
+   transforms overlap, and a transform's passes follow one another while its
+   data may still be in L2), and the caller's stream waits for all of them.
+   Capturable into one CUDA graph like the persistent launch.  The streams
+   and events are created on the first execute (on the current device, which
+   must be the plans' device; else TFFT_EINVAL) and destroyed with the batch.
+   For TFFT_BATCH_PERSISTENT `nstreams` is ignored. */
+int tfft_batch_set_executor(tfft_batch batch, int executor, int nstreams);
+/* The executor in use and its stream count (0 for the persistent kernel). */
+int tfft_batch_executor(tfft_batch batch, int *executor, int *nstreams);
 
 /*
  * Fused transform whose scratch lives in a fixed device array inside this

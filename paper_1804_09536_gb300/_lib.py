@@ -17,6 +17,8 @@ TFFT_FORWARD = -1
 TFFT_BACKWARD = 1
 TFFT_C2C = 0
 TFFT_R2C = 1
+TFFT_BATCH_PERSISTENT = 0
+TFFT_BATCH_STREAMS = 1
 TFFT_FP32 = 0
 TFFT_TC_BF16X3 = 1
 TFFT_TC_FP16X3 = 2
@@ -74,6 +76,8 @@ SIGNATURES = {
     "tfft_batch_segment": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "tfft_batch_set_variant": [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
     "tfft_batch_set_wait_limit": [_vp, ctypes.c_longlong],
+    "tfft_batch_set_executor": [_vp, ctypes.c_int, ctypes.c_int],
+    "tfft_batch_executor": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "tfft_plan_set_wait_limit": [_vp, ctypes.c_uint32],
     "tfft_batch_device_status": [_vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, _vp],
     "tfft_execute_noalloc": [_vp, ctypes.c_int, _vp, _vp, _vp],

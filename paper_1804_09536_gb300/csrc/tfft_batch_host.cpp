@@ -6,6 +6,8 @@
 
 namespace {
 
+constexpr int kMaxBatchStreams = 16;
+
 struct BatchSegH {
   int t, pass, kind, L, prev;
   int64_t ntiles;
@@ -41,6 +43,29 @@ struct tfft_batch_s {
   size_t state_bytes = 0, ctr_off = 0, seg_off = 0, cb_off = 0, map_off = 0;  // map_off: 2 tensor maps per segment
   int64_t nitems = 0;
   long long spin_limit = 4000000000LL;  // clock cycles (~2 s at 2 GHz)
+  // stream executor: transforms per forked stream, and the streams and events
+  // of the fork / join (created on the device of the first execute)
+  int executor = TFFT_BATCH_PERSISTENT;
+  int nstreams = 4;
+  std::vector<std::vector<int>> lanes;
+  struct Fork {
+    int device = -1;
+    std::vector<cudaStream_t> s;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t start = nullptr;
+  } fork;
+  void release_fork() {
+    if (fork.device < 0) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(fork.device);
+    for (cudaStream_t x : fork.s) cudaStreamDestroy(x);
+    for (cudaEvent_t x : fork.done) cudaEventDestroy(x);
+    if (fork.start) cudaEventDestroy(fork.start);
+    cudaSetDevice(cur);
+    fork = Fork{};
+  }
+  ~tfft_batch_s() { release_fork(); }
 };
 
 namespace {
@@ -180,7 +205,73 @@ int batch_upload(tfft_batch b, cudaStream_t st) {
   return TFFT_OK;
 }
 
-int batch_launch(tfft_batch b, cudaStream_t st) {
+// Stream executor: transforms, longest first, each to the stream with the
+// fewest elements so far.
+void batch_lanes(tfft_batch b) {
+  const int n = (int)b->plans.size();
+  const int K = std::max(1, std::min(b->nstreams, n));
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->plans[x]->nelems > b->plans[y]->nelems; });
+  std::vector<int64_t> load(K, 0);
+  b->lanes.assign(K, {});
+  for (int t : order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->lanes[j].push_back(t);
+    load[j] += b->plans[t]->nelems;
+  }
+}
+
+int ensure_fork(tfft_batch b) {
+  const int dev = current_device();
+  const size_t K = b->lanes.size();
+  if (b->fork.device == dev && b->fork.s.size() >= K) return TFFT_OK;
+  b->release_fork();
+  b->fork.device = dev;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork.start, cudaEventDisableTiming);
+  for (size_t j = 0; j < K && e == cudaSuccess; ++j) {
+    cudaStream_t x = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->fork.s.push_back(x);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->fork.done.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    b->release_fork();
+    return cuda_fail(e, "creating the batch's fork streams");
+  }
+  return TFFT_OK;
+}
+
+// Every transform's fused passes as its plan's own kernels, the transforms of
+// lane j in order on forked stream j; the caller's stream waits for all.
+int batch_launch_streams(tfft_batch b, cudaStream_t st) {
+  const int dev = current_device();
+  for (tfft_plan p : b->plans)
+    if (p->device != dev) return fail(TFFT_EINVAL, "a plan of the batch is bound on another device than the current one");
+  if (b->lanes.empty()) batch_lanes(b);
+  int rc = ensure_fork(b);
+  if (rc) return rc;
+  cudaError_t e = cudaEventRecord(b->fork.start, st);
+  for (size_t j = 0; j < b->lanes.size() && e == cudaSuccess; ++j) {
+    cudaStream_t x = b->fork.s[j];
+    e = cudaStreamWaitEvent(x, b->fork.start, 0);
+    for (int t : b->lanes[j]) {
+      if (e != cudaSuccess) break;
+      void* bufs[4] = {b->ins[t], b->outs[t], b->works[t], nullptr};
+      for (const Step& s : b->steps[t])
+        if ((rc = launch_step(b->plans[t], s, bufs, x))) return rc;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork.done[j], x);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->fork.done[j], 0);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "batch fork / join");
+  return TFFT_OK;
+}
+
+int batch_launch_persistent(tfft_batch b, cudaStream_t st) {
   const size_t ctr_bytes = align_up(16 + b->segs.size() * sizeof(int), 256);
   cudaError_t e = cudaMemsetAsync(b->d_state + b->ctr_off, 0, ctr_bytes, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync (batch counters)");
@@ -198,6 +289,24 @@ int batch_launch(tfft_batch b, cudaStream_t st) {
   e = launch_batch(a, grid, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return TFFT_OK;
+}
+
+int batch_launch(tfft_batch b, cudaStream_t st) {
+  return b->executor == TFFT_BATCH_STREAMS ? batch_launch_streams(b, st) : batch_launch_persistent(b, st);
+}
+
+// Mean ms of `reps` launches of the current executor (after one warm-up).
+int time_batch(tfft_batch b, int reps, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float& ms) {
+  int rc = batch_launch(b, st);
+  if (rc) return rc;
+  cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && !rc; ++r) rc = batch_launch(b, st);
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "timing the batch");
+  cudaEventElapsedTime(&ms, e0, e1);
+  ms /= (float)reps;
+  return rc;
 }
 
 }  // namespace
@@ -358,6 +467,8 @@ int tfft_batch_autotune(tfft_batch b, int reps, void* stream) {
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
       return fail(TFFT_ECUDA, "cudaEventCreate");
     int rc = TFFT_OK;
+    const int exec0 = b->executor;
+    b->executor = TFFT_BATCH_PERSISTENT;  // tile variants: the persistent kernel's
     for (auto& kv : b->choice) {
       const std::vector<int> cands = batch_candidates(kv.first.first, kv.first.second);
       auto hit = cached.find(kv.first);
@@ -386,12 +497,40 @@ int tfft_batch_autotune(tfft_batch b, int reps, void* stream) {
       kv.second = best_v;
       if (rc) break;
     }
+    // executor: the persistent kernel with the chosen tiles, or the stream
+    // executor with 1, 2, 3, 4, 6 or 8 streams, whichever runs the batch fastest
+    auto ex = cached.find({-1, -1});
+    if (!rc && ex != cached.end()) {
+      b->executor = ex->second >= 1 ? TFFT_BATCH_STREAMS : TFFT_BATCH_PERSISTENT;
+      if (ex->second >= 1) b->nstreams = std::min(ex->second, kMaxBatchStreams);
+      batch_lanes(b);
+    } else if (!rc) {
+      float best = 1e30f, ms = 0;
+      int best_k = 0;
+      if (!(rc = batch_upload(b, st)) && !(rc = time_batch(b, reps, st, e0, e1, ms))) best = ms;
+      b->executor = TFFT_BATCH_STREAMS;
+      for (int k : {1, 2, 3, 4, 6, 8}) {
+        if (rc || k > (int)b->plans.size()) break;
+        b->nstreams = k;
+        batch_lanes(b);
+        if ((rc = time_batch(b, reps, st, e0, e1, ms))) break;
+        if (ms < best) {
+          best = ms;
+          best_k = k;
+        }
+      }
+      b->executor = best_k ? TFFT_BATCH_STREAMS : TFFT_BATCH_PERSISTENT;
+      if (best_k) b->nstreams = best_k;
+      batch_lanes(b);
+    }
+    if (rc) b->executor = exec0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
     if (cache) {
       if (FILE* f = std::fopen(cache, "w")) {
         for (auto& kv : b->choice) std::fprintf(f, "%d %d %d\n", kv.first.first, kv.first.second, kv.second);
+        std::fprintf(f, "-1 -1 %d\n", b->executor == TFFT_BATCH_STREAMS ? b->nstreams : 0);
         std::fclose(f);
       }
     }
@@ -413,6 +552,29 @@ int tfft_batch_set_variant(tfft_batch b, int kind, int L, int variant, void* str
   });
 }
 
+int tfft_batch_set_executor(tfft_batch b, int executor, int nstreams) {
+  return guarded("tfft_batch_set_executor", [&]() -> int {
+    if (!b) return fail(TFFT_EINVAL, "batch is NULL");
+    if (executor != TFFT_BATCH_PERSISTENT && executor != TFFT_BATCH_STREAMS)
+      return fail(TFFT_EINVAL, "unknown batch executor");
+    if (executor == TFFT_BATCH_STREAMS && (nstreams < 1 || nstreams > kMaxBatchStreams))
+      return fail(TFFT_EINVAL, "nstreams must be in 1 .. 16");
+    b->executor = executor;
+    if (executor == TFFT_BATCH_STREAMS) {
+      b->nstreams = nstreams;
+      batch_lanes(b);
+    }
+    return TFFT_OK;
+  });
+}
+
+int tfft_batch_executor(tfft_batch b, int* executor, int* nstreams) {
+  if (!b || !executor || !nstreams) return fail(TFFT_EINVAL, "NULL argument");
+  *executor = b->executor;
+  *nstreams = b->executor == TFFT_BATCH_STREAMS ? (int)b->lanes.size() : 0;
+  return TFFT_OK;
+}
+
 int tfft_batch_set_wait_limit(tfft_batch b, long long cycles) {
   if (!b) return fail(TFFT_EINVAL, "batch is NULL");
   b->spin_limit = cycles > 0 ? cycles : 4000000000LL;
@@ -423,15 +585,25 @@ int tfft_batch_device_status(tfft_batch b, int* status, int reset, void* stream)
   if (!b || !status) return fail(TFFT_EINVAL, "NULL argument");
   if (!b->d_state) return fail(TFFT_ESTATE, "batch is not bound");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int v = 0;
-  cudaError_t e = cudaMemcpyAsync(&v, b->d_state, sizeof(int), cudaMemcpyDeviceToHost, st);
+  // the persistent kernel reports in the batch state, the stream executor's
+  // kernels in their plans' states: the status is the OR of all of them
+  std::vector<char*> words = {b->d_state};
+  for (tfft_plan p : b->plans)
+    if (p->d_state && std::find(words.begin(), words.end(), p->d_state) == words.end()) words.push_back(p->d_state);
+  std::vector<int> vals(words.size(), 0);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < words.size() && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(&vals[i], words[i], sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && reset) {
     const int zero = 0;
-    e = cudaMemcpyAsync(b->d_state, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    for (size_t i = 0; i < words.size() && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(words[i], &zero, sizeof(int), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
-  if (e != cudaSuccess) return cuda_fail(e, "reading the batch status word");
+  if (e != cudaSuccess) return cuda_fail(e, "reading the batch status words");
+  int v = 0;
+  for (int x : vals) v |= x;
   *status = v;
   return TFFT_OK;
 }

@@ -74,13 +74,20 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
 #pragma unroll
         for (int r = 0; r < RL; ++r) sl[padp<P>(jt + q * T + r * (L / RL))] = v[q * RL + r];
     line_sync<T>();
-    for (int k = jt; k <= L; k += T) {
-      const float2 zk = sl[padp<P>(k == L ? 0 : k)];
+    // outputs k and L - k together: with e, o of k, X[k] = e + o and, as
+    // w^(L-k) = -conj(w^k) and the roles of Z[k], Z[L-k] swap,
+    // X[L-k] = conj(e - o) -- one pair of shared loads and one twiddle for two
+    // outputs (k = 0 gives X[0] and X[L]; k = L/2 is its own partner)
+    for (int k = jt; k <= L / 2; k += T) {
+      const float2 zk = sl[padp<P>(k)];
       const float2 zm = sl[padp<P>(k == 0 ? 0 : L - k)];
       const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));   // (Z[k] + conj Z[L-k]) / 2
       const float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));   // (Z[k] - conj Z[L-k]) / 2
       const float2 o = cmul(__ldg(&a.tw2[k]), mul_mi(d));                          // -i w^k d
-      if (act) dst[k] = cscale(cadd(e, o), a.scale);
+      if (act) {
+        dst[k] = cscale(cadd(e, o), a.scale);
+        if (2 * k != L) dst[L - k] = cscale(make_float2(e.x - o.x, o.y - e.y), a.scale);
+      }
     }
   }
 }
@@ -100,23 +107,40 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
     const float2* src = a.cin + line * a.cpitch;
     float2* dst = reinterpret_cast<float2*>(a.rout) + line * L;
     const int jt = opaque_tid_x();
-    // the L + 1 inputs: every load issued before the first shared store, so
+    // the L + 1 inputs as the pairs (X[k], X[L-k]), k <= L/2 (k = 0 pairs
+    // X[0] with X[L]): every load issued before the first shared store, so
     // that they are all in flight together
-    constexpr int NK = E + 1;  // ceil((L + 1) / T)
-    float2 xin[NK];
+    constexpr int NP = (L / 2) / T + 1;
+    float2 xa[NP], xb[NP];
 #pragma unroll
-    for (int i = 0; i < NK; ++i) {
+    for (int i = 0; i < NP; ++i) {
       const int k = jt + i * T;
-      xin[i] = (act && k <= L) ? src[k] : make_float2(0.f, 0.f);
+      const bool ok = act && k <= L / 2;
+      xa[i] = ok ? src[k] : make_float2(0.f, 0.f);
+      xb[i] = ok ? src[L - k] : make_float2(0.f, 0.f);
     }
     line_sync<T>();  // the previous line group is done with sl
+    // Z[k] and Z[L-k] of each pair: with e, q = i w^-k d of k, Z[k] = e + q
+    // and (w^-(L-k) = -w^k, the roles of X[k], X[L-k] swap) Z[L-k] =
+    // conj(e - q); stored conjugated (backward = conj o forward o conj).
+    // The imaginary parts of X[0] and X[L] are ignored; k = L/2 is its own
+    // partner.
 #pragma unroll
-    for (int i = 0; i < NK; ++i) {
+    for (int i = 0; i < NP; ++i) {
       const int k = jt + i * T;
-      if (k <= L) {
-        float2 x = xin[i];
-        if (k == 0 || k == L) x.y = 0.f;
-        sl[padp<P>(k)] = x;
+      if (k <= L / 2) {
+        float2 xk = xa[i], xm = xb[i];
+        if (k == 0) {
+          xk.y = 0.f;
+          xm.y = 0.f;
+        }
+        const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);      // X[k] + conj X[L-k]
+        const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);      // X[k] - conj X[L-k]
+        const float2 w = __ldg(&a.tw2[k]);
+        const float2 od = cmul(make_float2(w.x, -w.y), d);           // w^-k d
+        const float2 qv = make_float2(-od.y, od.x);                  // i w^-k d
+        sl[padp<P>(k)] = make_float2(e.x + qv.x, -(e.y + qv.y));     // conj Z[k]
+        if (k > 0 && 2 * k != L) sl[padp<P>(L - k)] = make_float2(e.x - qv.x, e.y - qv.y);  // conj Z[L-k]
       }
     }
     line_sync<T>();
@@ -131,14 +155,7 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int k = bf_exists<L, E, R>(jt, q) ? jt + q * T + r * (L / R) : 0;
-            const float2 xk = sl[padp<P>(k)];
-            const float2 xm = sl[padp<P>(L - k)];
-            const float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);      // X[k] + conj X[L-k]
-            const float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);      // X[k] - conj X[L-k]
-            const float2 w = __ldg(&a.tw2[k]);
-            const float2 od = cmul(make_float2(w.x, -w.y), d);           // w^-k d
-            const float2 z = make_float2(e.x - od.y, e.y + od.x);         // e + i w^-k d
-            v[q * R + r] = make_float2(z.x, -z.y);                        // backward = conj o forward o conj
+            v[q * R + r] = sl[padp<P>(k)];
           }
       } else {
         constexpr int Rp = radix_at<s - 1, Rs...>();

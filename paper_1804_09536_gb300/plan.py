@@ -375,6 +375,21 @@ class Batch:
         call("tfft_batch_variant", self._h, kind, L, ctypes.byref(v))
         return v.value
 
+    def set_executor(self, executor: str = "persistent", nstreams: int = 4):
+        """'persistent': one persistent kernel over every pass; 'streams': each
+        transform's own pass kernels, transforms dealt over `nstreams` forked
+        streams (tfft_batch_set_executor)."""
+        kind = {"persistent": _lib.TFFT_BATCH_PERSISTENT, "streams": _lib.TFFT_BATCH_STREAMS}[executor]
+        call("tfft_batch_set_executor", self._h, kind, int(nstreams))
+
+    @property
+    def executor(self):
+        """('persistent', 0) or ('streams', number of streams)."""
+        e = ctypes.c_int()
+        k = ctypes.c_int()
+        call("tfft_batch_executor", self._h, ctypes.byref(e), ctypes.byref(k))
+        return ("streams" if e.value == _lib.TFFT_BATCH_STREAMS else "persistent", k.value)
+
     def set_wait_limit(self, cycles: int):
         call("tfft_batch_set_wait_limit", self._h, int(cycles))
 

@@ -147,6 +147,39 @@ def test_batch_issue_order(lib, which):
     assert order == want
 
 
+def test_batch_executor_choice(lib):
+    """The stream executor is chosen and queried on the host (no GPU work):
+    stream counts are clipped to the transform count, bad values rejected,
+    and the persistent kernel stays the default."""
+    from paper_1804_09536_gb300.plan import Plan
+    plans = [Plan(sh, gr, bind=False) for sh, gr in [((64, 64, 64), (2, 2)), ((96, 96, 96), (2, 2)),
+                                                      ((128, 128, 128), (2, 4))]]
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    b = ctypes.c_void_p()
+    assert lib.tfft_batch_create(ctypes.byref(b), len(plans), arr, -1) == 0
+    e, k = ctypes.c_int(), ctypes.c_int()
+    try:
+        assert lib.tfft_batch_executor(b, ctypes.byref(e), ctypes.byref(k)) == 0
+        assert (e.value, k.value) == (0, 0)
+        assert lib.tfft_batch_set_executor(b, 1, 2) == 0
+        assert lib.tfft_batch_executor(b, ctypes.byref(e), ctypes.byref(k)) == 0
+        assert (e.value, k.value) == (1, 2)
+        assert lib.tfft_batch_set_executor(b, 1, 8) == 0     # more streams than transforms
+        assert lib.tfft_batch_executor(b, ctypes.byref(e), ctypes.byref(k)) == 0
+        assert (e.value, k.value) == (1, 3)
+        assert lib.tfft_batch_set_executor(b, 1, 0) == 1
+        assert lib.tfft_batch_set_executor(b, 1, 17) == 1
+        assert lib.tfft_batch_set_executor(b, 2, 1) == 1
+        assert lib.tfft_batch_set_executor(b, 0, 0) == 0
+        assert lib.tfft_batch_executor(b, ctypes.byref(e), ctypes.byref(k)) == 0
+        assert (e.value, k.value) == (0, 0)
+        # executing an unbound batch is refused before any GPU work
+        assert lib.tfft_batch_set_executor(b, 1, 2) == 0
+        assert lib.tfft_batch_execute(b, None) == 6
+    finally:
+        lib.tfft_batch_destroy(b)
+
+
 @pytest.mark.parametrize("shape,grid,c0,nc", [((512, 512, 512), (4, 8), 33, 224),
                                                ((64, 128, 512), (4, 8), 33, 224),
                                                ((128, 64, 256), (2, 4), 33, 96),

@@ -150,3 +150,77 @@ def test_batch_tma_tiles_match_standalone(cuda_device):
     assert b.device_status() == 0
     for k in range(len(SMALL)):
         assert torch.equal(b.outs[k], refs[k]), k
+
+
+@pytest.mark.parametrize("nstreams", [1, 3, 8])
+def test_stream_executor_matches_standalone(cuda_device, nstreams):
+    """The stream executor runs each transform's own pass kernels on forked
+    streams: the same bits as the plans' standalone forwards, eagerly and
+    replayed from a CUDA graph (which captures the fork and the join)."""
+    from paper_1804_09536_gb300.plan import Batch
+    plans = _plans(SMALL, cuda_device)
+    b = Batch(plans, sign=-1)
+    b.set_executor("streams", nstreams)
+    assert b.executor == ("streams", min(nstreams, len(SMALL)))
+    for k, (shape, grid) in enumerate(SMALL):
+        b.ins[k].copy_(to_dev(R.scatter(inputs.uniform_complex(shape, seed=200 + k).numpy(), grid, 0),
+                              cuda_device))
+    refs = [plans[k].forward(b.ins[k]) for k in range(len(SMALL))]
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    for k in range(len(SMALL)):
+        assert torch.equal(b.outs[k], refs[k]), k
+    g = b.graph()
+    for o in b.outs:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for k in range(len(SMALL)):
+        assert torch.equal(b.outs[k], refs[k]), k
+
+
+def test_stream_executor_reports_plan_status(cuda_device):
+    """A copy wait that expires inside a transform run by the stream executor
+    lands in its plan's status word, which the batch status ORs in."""
+    from paper_1804_09536_gb300.plan import Batch
+    problems = [((64, 64, 64), (2, 2)), ((128, 128, 128), (2, 4))]
+    plans = _plans(problems, cuda_device)
+    b = Batch(plans, sign=-1)
+    b.set_executor("streams", 2)
+    for k, (shape, grid) in enumerate(problems):
+        b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(shape, seed=k).to(cuda_device), 0))
+    names = [n for n, _ in plans[1].launch_info(-1)]
+    assert any("tma" in n for n in names), names
+    plans[1].set_wait_limit(1)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status(reset=True) == 1
+    assert plans[1].device_status() == 0
+    plans[1].set_wait_limit(0)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+
+
+def test_autotune_picks_an_executor(cuda_device):
+    """Autotuning times the persistent kernel against the stream executor and
+    keeps the faster; either way the results stay the oracle's."""
+    from paper_1804_09536_gb300.plan import Batch
+    plans = _plans(SMALL, cuda_device)
+    b = Batch(plans, sign=-1)
+    xs = [inputs.uniform_complex(shape, seed=300 + k).numpy() for k, (shape, _) in enumerate(SMALL)]
+    for k, (shape, grid) in enumerate(SMALL):
+        b.ins[k].copy_(to_dev(R.scatter(xs[k], grid, 0), cuda_device))
+    keep = [t.clone() for t in b.ins]
+    b.autotune(reps=2)
+    kind, n = b.executor
+    assert (kind == "persistent" and n == 0) or (kind == "streams" and 1 <= n <= 8)
+    for t, k in zip(b.ins, keep):
+        t.copy_(k)
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    for k, (shape, grid) in enumerate(SMALL):
+        want = dft.distributed_forward(R.scatter(xs[k], grid, 0).astype(np.complex128), shape, grid)
+        assert rel_l2(b.outs[k].cpu().numpy(), want) <= RTOL_FP32, k
