@@ -117,26 +117,36 @@ class ClockSampler:
 
 def _traffic_per_launch(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel source is unchanged since the counters were taken."""
+    sources that define that kernel are unchanged since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernels_sha256_16") != kernel_source_hash():
+        k = rec["kernels"][kernel]
+        if k["sources_sha256_16"] != kernel_source_hash(k["sources"]):
             return None
-        return rec["per_launch_bytes"].get(kernel)
+        return k["per_launch_bytes"]
     except Exception:
         return None
 
 
-def kernel_source_hash() -> str:
-    """sha256 (16 hex digits) over every CUDA source and header of the library."""
+# The device sources each measured kernel is compiled from (its translation
+# unit, the headers it includes, and the argument structs it is passed).
+KERNEL_SOURCES = {
+    "fft_strided_tma_L512": ["tfft_tma.cu", "tfft_tma.cuh", "tfft_tiles.cuh", "tfft_common.cuh",
+                             "tfft_internal.h", "tfft_device_cache.h"],
+    "fft_contig_L512": ["tfft_spec.cu", "tfft_spec_table.h", "tfft_tiles.cuh", "tfft_common.cuh",
+                        "tfft_internal.h", "tfft_device_cache.h"],
+}
+
+
+def kernel_source_hash(names) -> str:
+    """sha256 (16 hex digits) over the named files of the library's csrc/."""
     csrc = os.path.join(ROOT, "paper_1804_09536_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in sorted(names):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 

@@ -248,7 +248,11 @@ cudaError_t run_strided_tma(const StridedArgs& a, const Geo& geo, cudaStream_t s
 
 // Strided TMA variants: length, elements per thread, tile width, radices.
 // The first row of a length is its default; tma_strided_variant() can pick
-// another (autotuning).
+// another (autotuning).  256: 16-column tiles at two CTAs per SM beat 32
+// columns at one (256^3 on 4 x 8 / 2 x 2 / 2 x 4: 0.048 vs 0.052 ms per pass;
+// the 48-transform batch 1.96 vs 2.01 ms); 8 elements per thread (radices
+// 8, 8, 4) took 0.057 ms.  512: 8-column tiles at two CTAs per SM took 0.361
+// vs 0.336 ms per 512^3 pass (64-byte rows).
 #define TFFT_TMA_STRIDED(X)     \
   X(64, 8, 32, 8, 8)            \
   X(96, 12, 32, 4, 4, 3, 2)     \
@@ -256,6 +260,7 @@ cudaError_t run_strided_tma(const StridedArgs& a, const Geo& geo, cudaStream_t s
   X(160, 20, 16, 5, 4, 4, 2)    \
   X(384, 24, 16, 8, 8, 3, 2)    \
   X(1024, 32, 8, 32, 32)        \
+  X(256, 16, 16, 16, 16)        \
   X(256, 16, 32, 16, 16)        \
   X(512, 32, 16, 32, 16)        \
   X(512, 16, 16, 8, 8, 8)
