@@ -35,9 +35,10 @@ def test_execute_host_c2c_matches_device_path(cuda_device, signs):
         assert rel_l2(h_out[0].numpy(), h_in[0].numpy()) <= RTOL_FP32
 
 
-def test_execute_host_r2c(cuda_device):
+@pytest.mark.parametrize("shape,grid", [((16, 32, 64), (4,)),
+                                        ((16, 64, 256), (2, 4))])   # padded stage 0, column window
+def test_execute_host_r2c(cuda_device, shape, grid):
     from paper_1804_09536_gb300.plan import Plan
-    shape, grid = (16, 32, 64), (4,)
     p = Plan(shape, grid, kind="r2c", device=cuda_device)
     xs = [p.scatter(inputs.normal_real(shape, seed=30 + k).to(cuda_device), 0, real=True) for k in range(3)]
     h_in = [_pinned(x.cpu()) for x in xs]

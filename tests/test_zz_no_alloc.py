@@ -38,7 +38,8 @@ def _same_bits(a, b):
 
 @pytest.mark.parametrize("shape,grid,kind", [((32, 32, 32), (2, 2), "c2c"),
                                              ((64, 64, 64), (2, 4), "c2c"),
-                                             ((16, 32, 64), (4,), "r2c")])
+                                             ((16, 32, 64), (4,), "r2c"),
+                                             ((16, 64, 256), (2, 4), "r2c")])   # padded stage 0, column window
 def test_noalloc_matches_execute(cuda_device, lib, shape, grid, kind):
     from paper_1804_09536_gb300 import inputs
     from paper_1804_09536_gb300.plan import Plan
