@@ -282,7 +282,13 @@ int tfft_plan_num_launches(tfft_plan plan, int sign, int mode, int *nlaunches);
  * Launch `index` of tfft_execute() in a direction and mode: the kernel's
  * name (NUL-terminated, truncated to name_len) and its algorithmic bytes --
  * one read and one write of every element it moves (complex64), the figure
- * a roofline divides by the launch's duration.
+ * a roofline divides by the launch's duration.  Names: fft_contig_L<n>,
+ * fft_strided_L<n> (plain tiles), fft_strided_tma_L<n> (TMA-staged tiles),
+ * ..._tma_groups_... (rank groups of an uneven layout), ..._tma_window_...
+ * (a column window of a real-to-complex pencil plan; the next launch is the
+ * plain kernel over the remaining columns, and each reports the bytes of
+ * its own columns), ..._tc_bf16x3 / _tc_fp16x3 (tensor-core stage),
+ * fft_strided_bluestein_L<n>, fft_r2c_L<n> / fft_c2r_L<n>, box_copy.
  */
 int tfft_plan_launch_info(tfft_plan plan, int sign, int mode, int index, char *name,
                           int name_len, int64_t *bytes);
