@@ -255,19 +255,29 @@ int batch_launch_streams(tfft_batch b, cudaStream_t st) {
   int rc = ensure_fork(b);
   if (rc) return rc;
   cudaError_t e = cudaEventRecord(b->fork.start, st);
-  for (size_t j = 0; j < b->lanes.size() && e == cudaSuccess; ++j) {
+  if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+  // every forked stream is joined back even when a launch fails, so that a
+  // stream capture in progress stays well formed (its end reports the error)
+  cudaError_t ej = cudaSuccess;
+  for (size_t j = 0; j < b->lanes.size(); ++j) {
     cudaStream_t x = b->fork.s[j];
-    e = cudaStreamWaitEvent(x, b->fork.start, 0);
+    cudaError_t ef = cudaStreamWaitEvent(x, b->fork.start, 0);
+    if (ef != cudaSuccess) {
+      if (ej == cudaSuccess) ej = ef;
+      continue;
+    }
     for (int t : b->lanes[j]) {
-      if (e != cudaSuccess) break;
+      if (rc) break;
       void* bufs[4] = {b->ins[t], b->outs[t], b->works[t], nullptr};
       for (const Step& s : b->steps[t])
-        if ((rc = launch_step(b->plans[t], s, bufs, x))) return rc;
+        if ((rc = launch_step(b->plans[t], s, bufs, x))) break;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(b->fork.done[j], x);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->fork.done[j], 0);
+    cudaError_t e2 = cudaEventRecord(b->fork.done[j], x);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, b->fork.done[j], 0);
+    if (e2 != cudaSuccess && ej == cudaSuccess) ej = e2;
   }
-  if (e != cudaSuccess) return cuda_fail(e, "batch fork / join");
+  if (rc) return rc;
+  if (ej != cudaSuccess) return cuda_fail(ej, "batch fork / join");
   return TFFT_OK;
 }
 
