@@ -322,6 +322,40 @@ def test_r2c_column_window_passes(cuda_device, shape, grid):
     assert rel_l2(yu.cpu().numpy(), want) <= RTOL_FP32
 
 
+def test_r2c_window_plan_replays_from_a_cuda_graph(cuda_device):
+    """The column-window passes (tensor maps encoded at launch, two launches on
+    one pair of buffers) captured in a CUDA graph and replayed: the same bits
+    as the eager forward and inverse."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (64, 128, 512), (4, 8)
+    p = Plan(shape, grid, kind="r2c", device=cuda_device)
+    x = to_dev(R.scatter(inputs.normal_real(shape, seed=5).numpy(), grid, 0), cuda_device)
+    y_ref = p.forward(x)
+    z_ref = p.inverse(y_ref.clone())
+    y = p.empty_stage(p.g)
+    yi = p.empty_stage(p.g)
+    z = p.empty_stage(0, real=True)
+    work = p.workspace("fused")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.execute(-1, x, y, "fused", work)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        p.execute(-1, x, y, "fused", work)
+        yi.copy_(y)
+        p.execute(1, yi, z, "fused", work)
+    for t in (y, z):
+        t.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    assert torch.equal(y, y_ref)
+    assert torch.equal(z, z_ref)
+
+
 R2C_CASES = [
     ((8, 12, 480), (2, 2)),          # half-length 240 (2.3.5)
     ((4, 8, 2048), (2, 2)),          # half-length 1024
