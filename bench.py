@@ -602,6 +602,32 @@ def profile_workload(args, dev):
                       "ms_per_step": a.elapsed_time(e) / args.steps}))
 
 
+def graph_replay_ms(one, steps, barrier):
+    """ms per replay of `one` captured in a CUDA graph (the same launches without
+    the host's per-launch cost), timed with CUDA events after warm-up replays."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        one()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        one()
+    for _ in range(3):
+        g.replay()
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        g.replay()
+    b.record()
+    barrier()
+    return a.elapsed_time(b) / steps
+
+
 def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), grid=(8,)):
     """Real-to-complex forward + inverse on a virtual grid (default: 256^3 on an
     8-rank slab, output 256 x 256 x 129), fused and packed; ms per step and the
@@ -633,6 +659,7 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), gri
         out[mode] = a.elapsed_time(b) / steps
         if mode == "fused":
             nbytes = sum(n for _, n in p.launch_info(-1, mode) + p.launch_info(+1, mode))
+            out["graph"] = graph_replay_ms(one, steps, barrier)
     # every launch of the fused path on its own (CUDA events around each launch)
     wf = p.workspace("fused")
 
@@ -653,8 +680,12 @@ def r2c_slab(plan_cls, dev, steps, barrier, tma=True, shape=(256, 256, 256), gri
             "fused_vs_packed_speedup": round(out["packed"] / out["fused"], 3),
             "GFLOPs": round(2 * 2.5 * n * math.log2(n) / (out["fused"] * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (out["fused"] * 1e-3) / 1e9 / peak, 4),
+            "fused_graph_ms": round(out["graph"], 4),
+            "hbm_frac_graph": round(nbytes / (out["graph"] * 1e-3) / 1e9 / peak, 4),
             "kernels": kernels,
-            "note": "c2r overwrites its input; the forward output is reused as the inverse's input"}
+            "note": "c2r overwrites its input; the forward output is reused as the inverse's input; "
+                    "fused_ms: launches from the host each step; fused_graph_ms: the same step "
+                    "replayed from a CUDA graph"}
 
 
 def appendix_a(plan_cls, dev, steps, barrier, shape=(42, 127, 256), grid=(3, 4)):
@@ -688,6 +719,7 @@ def appendix_a(plan_cls, dev, steps, barrier, shape=(42, 127, 256), grid=(3, 4))
     b.record()
     barrier()
     ms = a.elapsed_time(b) / steps
+    ms_graph = graph_replay_ms(step, steps, barrier)
     kernels = per_launch_times(p, step, "fused", w, steps, barrier, stream)
     err = float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x))
     n = math.prod(shape)
@@ -698,6 +730,8 @@ def appendix_a(plan_cls, dev, steps, barrier, shape=(42, 127, 256), grid=(3, 4))
                         f"Bluestein), virtual grid {'x'.join(map(str, grid))}, forward+inverse, fused; "
                         f"{mib:.1f} MiB per stage buffer ({'L2-resident' if 8 * n < 129e6 else 'larger than L2'})",
             "ms_per_step": round(ms, 4), "hbm_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+            "graph_ms_per_step": round(ms_graph, 4),
+            "hbm_frac_graph": round(nbytes / (ms_graph * 1e-3) / 1e9 / peak, 4),
             "kernels": kernels, "round_trip_rel_l2": err}
 
 
