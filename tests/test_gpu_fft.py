@@ -222,6 +222,25 @@ def test_norm_backward_flag(cuda_device):
     assert rel_l2(y, want) <= RTOL_FP32
 
 
+def test_norm_backward_r2c_window_plan(cuda_device):
+    """TFFT_NORM_BACKWARD on a real-to-complex plan with a column window: the
+    unscaled forward, and the 1/N of the inverse on its complex-to-real pass
+    after the two column ranges of the gathering pass."""
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (16, 512, 120), (2, 4)
+    p = Plan(shape, grid, kind="r2c", norm="backward", device=cuda_device)
+    assert sum("tma_window" in n for n, _ in p.launch_info(+1)) == 1
+    x = inputs.normal_real(shape, seed=6).numpy()
+    b0 = R.scatter(x, grid, 0)
+    y = p.forward(to_dev(b0, cuda_device))
+    want = dft.distributed_rfft_forward(b0.astype(np.float64), shape, grid) * math.prod(shape)
+    assert rel_l2(y.cpu().numpy(), want) <= RTOL_FP32
+    z = p.inverse(y.clone())
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    assert rel_l2(z.cpu().numpy(), b0) <= RTOL_FP32
+
+
 @pytest.mark.slow
 def test_full_size_512_pencil_sampled(cuda_device):
     """The bench workload (512^3, 4 x 8, launch configuration of bench.py): sampled
