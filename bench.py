@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -140,13 +141,22 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and blank lines (so that editing a
+    comment does not void a record taken on the same code)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def kernel_source_hash(names) -> str:
-    """sha256 (16 hex digits) over the named files of the library's csrc/."""
+    """sha256 (16 hex digits) over the code (comments stripped) of the named
+    files of the library's csrc/."""
     csrc = os.path.join(ROOT, "paper_1804_09536_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(names):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(name.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

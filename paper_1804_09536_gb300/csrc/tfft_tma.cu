@@ -23,6 +23,11 @@
 // last tile of a rank may be partial -- the copy fills the missing columns
 // with zeros and the store skips them.
 //
+// The equal-block view also serves a column window of the innermost axis
+// (TmaGeo::c0): the gathering pass of a real-to-complex pencil plan reads a
+// padded internal stage 0 and writes the last stage's ranks of one even
+// width, both described from the window's first column on.
+//
 // Every wait on an mbarrier is bounded: on expiry the CTA records
 // TFFT_DEVICE_ETIMEOUT in the plan's status word and leaves.
 #include "tfft_tiles.cuh"
