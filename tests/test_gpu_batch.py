@@ -224,3 +224,27 @@ def test_autotune_picks_an_executor(cuda_device):
     for k, (shape, grid) in enumerate(SMALL):
         want = dft.distributed_forward(R.scatter(xs[k], grid, 0).astype(np.complex128), shape, grid)
         assert rel_l2(b.outs[k].cpu().numpy(), want) <= RTOL_FP32, k
+
+
+@pytest.mark.parametrize("sign", [-1, 1])
+def test_stream_executor_without_workspaces(cuda_device, sign):
+    """Inputs as scratch (no workspaces, keep_input=False), both directions, one
+    stream per transform and more streams than transforms: the stream executor
+    still matches the plans' standalone transforms bit for bit."""
+    from paper_1804_09536_gb300.plan import Batch
+    probs = SMALL[:3]
+    plans = _plans(probs, cuda_device)
+    b = Batch(plans, sign=sign, keep_input=False)
+    b.set_executor("streams", 16)
+    assert b.executor == ("streams", 3)
+    xs = []
+    for k, (shape, grid) in enumerate(probs):
+        st = 0 if sign < 0 else len(grid)
+        xs.append(to_dev(R.scatter(inputs.uniform_complex(shape, seed=400 + k).numpy(), grid, st), cuda_device))
+        b.ins[k].copy_(xs[k])
+    refs = [(p.forward(x) if sign < 0 else p.inverse(x)) for p, x in zip(plans, xs)]
+    b.execute()
+    torch.cuda.synchronize()
+    assert b.device_status() == 0
+    for k in range(len(probs)):
+        assert torch.equal(b.outs[k], refs[k]), k
