@@ -272,10 +272,13 @@ def run_ours(args):
             print(json.dumps({"profile_only": True, "workload": WORKLOAD, "ms_per_step": ms_step,
                               "kernels": {n: statistics.fmean(r["ms"]) for n, r in kern.items()}}))
         return
+    # the same step replayed from a CUDA graph, without the per-launch events
+    # (outside the headline timing; reported beside it)
+    ksteps = max(3, min(args.steps, 20))
+    ms_graph = graph_replay_ms(lambda: step(), ksteps, barrier)
     # comparison paths, same protocol, fewer steps (outside the headline timing):
     # the whole step, then every launch on its own (events around each launch)
     extra, extra_kernels = {}, {}
-    ksteps = max(3, min(args.steps, 20))
     for mode in ("unfused", "packed"):
         w2 = plan.workspace(mode)
         for _ in range(2):
@@ -369,6 +372,7 @@ def run_ours(args):
         "ms_per_step": round(ms_step, 4),
         "ms_step_min": round(min(per_step), 4),
         "ms_step_median": round(statistics.median(per_step), 4),
+        "graph_ms_per_step": round(ms_graph, 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
