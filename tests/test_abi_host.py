@@ -220,3 +220,37 @@ def test_r2c_column_window_plan(lib, shape, grid, c0, nc):
     assert not any("window" in n for n, _ in q.launch_info(-1))
     c = Plan(shape, grid, kind="r2c", bind=False, precision="bf16x3")
     assert not any("window" in n for n, _ in c.launch_info(-1))
+
+
+def test_launch_bytes_account_for_every_pass(lib):
+    """Host-side roofline accounting over a seeded sweep of plans: the fused
+    path's launches report one read and one write of every element per pass
+    (a real-to-complex pass: the real array plus the complex half), whatever
+    the column splits (windows, rank groups, plain remainders); the fused
+    workspace is at least one complex stage and at most 1/16 larger."""
+    import random
+    from paper_1804_09536_gb300.plan import Plan
+    from paper_1804_09536_gb300._lib import TfftError
+    rng = random.Random(5)
+    lens = [8, 16, 24, 32, 48, 60, 64, 96, 120, 128, 160, 192, 240, 256, 512]
+    checked = 0
+    while checked < 60:
+        d = rng.choice([2, 3, 3])
+        shape = tuple(rng.choice(lens) for _ in range(d))
+        grid = tuple(rng.choice([1, 2, 3, 4, 8]) for _ in range(rng.randint(1, d - 1)))
+        kind = rng.choice(["c2c", "r2c"])
+        try:
+            p = Plan(shape, grid, kind=kind, bind=False)
+            info = p.launch_info(-1) + p.launch_info(1)
+        except TfftError:
+            continue
+        n = math.prod(shape)
+        nc = n if kind == "c2c" else n // shape[-1] * (shape[-1] // 2 + 1)
+        want = 2 * d * 16 * nc
+        if kind == "r2c":
+            want += 2 * (4 * n + 8 * nc) - 2 * 16 * nc
+        assert sum(b for _, b in info) == want, (shape, grid, kind, info)
+        ws = p.workspace_bytes("fused")
+        if kind == "r2c":
+            assert 8 * nc <= ws <= 8 * nc + 8 * nc // 16 + 64, (shape, grid, ws)
+        checked += 1
