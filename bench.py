@@ -886,7 +886,10 @@ def batch48(dev, steps, barrier, autotune=True):
     from paper_1804_09536_gb300 import inputs
     from paper_1804_09536_gb300.plan import Batch, Plan
     problems = inputs.batch_problems(48, seed=0)
-    plans = [Plan(sh, gr, device=dev) for sh, gr in problems]
+    # graphs=False: the per-plan baselines below launch every kernel directly
+    # (the fastest way to run 48 different plans one after the other; a graph
+    # per plan adds a graph launch per transform)
+    plans = [Plan(sh, gr, device=dev, graphs=False) for sh, gr in problems]
     b = Batch(plans, sign=-1)
     for k, (sh, gr) in enumerate(problems):
         b.ins[k].copy_(plans[k].scatter(inputs.uniform_complex(sh, seed=k).to(dev), 0))

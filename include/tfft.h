@@ -75,7 +75,8 @@ enum { TFFT_FP32 = 0, TFFT_TC_BF16X3 = 1, TFFT_TC_FP16X3 = 2 };
 enum {
   TFFT_NORM_FORWARD = 0,
   TFFT_NORM_BACKWARD = 4,
-  TFFT_NO_TMA = 8 /* plain load/store passes even where the TMA-staged ones apply */
+  TFFT_NO_TMA = 8, /* plain load/store passes even where the TMA-staged ones apply */
+  TFFT_NO_GRAPH = 16 /* tfft_execute never replays captured launches (see tfft_execute) */
 };
 /* execution modes of tfft_execute */
 enum {
@@ -115,7 +116,7 @@ int tfft_decompose(int64_t N, int64_t M, int64_t p, int64_t *n, int64_t *s);
  * is taken as given, no dims-create balancing).  kind: TFFT_C2C or TFFT_R2C
  * (real input, Hermitian half on the last axis; N[d-1] even).  precision:
  * TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3.  flags: TFFT_NORM_FORWARD or
- * TFFT_NORM_BACKWARD, optionally | TFFT_NO_TMA.
+ * TFFT_NORM_BACKWARD, optionally | TFFT_NO_TMA | TFFT_NO_GRAPH.
  * Complex lengths that factor into 2, 3 and 5 (<= 4096) run mixed-radix
  * Stockham passes; any other complex length <= 2048 runs Bluestein's
  * convolution form of the DFT (two power-of-two FFTs of length >= 2N - 1 with
@@ -198,6 +199,16 @@ int tfft_partial(tfft_plan plan, int stage, int axis, int sign, void *inout, voi
  * tfft_plan_workspace_bytes().  When work is NULL in TFFT_MODE_FUSED C2C the
  * input buffer is used as scratch; a complex-to-real backward always
  * overwrites its input.  in and out must not overlap.
+ * Repeated calls: the second call with the same direction, mode, buffers
+ * (and, for the adjoint and loss calls, the same coefficient) captures its
+ * launches into a CUDA graph on a stream of the plan's own, and that call
+ * and every later identical one launch the graph on `stream` instead -- the
+ * same kernels with the same arguments, without the per-launch host cost
+ * (a few microseconds per kernel).  The plan keeps at most 8 such graphs
+ * (least recently used dropped) and destroys them with the plan; launch
+ * events (tfft_plan_set_launch_events) and TFFT_NO_GRAPH turn it off.  A
+ * caller that frees a buffer and gets the same address back for a new one
+ * simply replays the same launches on it.
  */
 int tfft_execute(tfft_plan plan, int sign, int mode, const void *in, void *out, void *work,
                  size_t work_bytes, void *stream);

@@ -25,6 +25,7 @@ TFFT_TC_FP16X3 = 2
 TFFT_NORM_FORWARD = 0
 TFFT_NORM_BACKWARD = 4
 TFFT_NO_TMA = 8
+TFFT_NO_GRAPH = 16
 TFFT_MODE_FUSED = 0
 TFFT_MODE_UNFUSED = 1
 TFFT_MODE_PACKED = 2

@@ -463,7 +463,73 @@ int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void*
   if (!p->events.empty() && p->events.size() < steps.size() + 1)
     return fail(TFFT_EINVAL, "fewer launch events than launches + 1");
   void* bufs[4] = {const_cast<void*>(in), out, w0, w1};
-  return run_steps(p, steps, bufs, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!p->events.empty() || (p->flags & TFFT_NO_GRAPH)) return run_steps(p, steps, bufs, st);
+  return run_steps_cached(p, tfft_plan_s::GraphKey{key, mode, in, out, w0, w1, coef, factor, p->wait_limit}, steps,
+                          bufs, st);
+}
+
+// run_steps through the plan's graph cache (see tfft_execute): the first call
+// of a key launches directly, the second captures the launches on the plan's
+// capture stream and instantiates them, that call and later ones launch the
+// graph on `st`.  A stream already being captured by the caller, or a failed
+// capture, launches directly.
+int run_steps_cached(tfft_plan p, const tfft_plan_s::GraphKey& k, const std::vector<Step>& steps, void* const* bufs,
+                     cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return run_steps(p, steps, bufs, st);
+  }
+  if (cs != cudaStreamCaptureStatusNone) return run_steps(p, steps, bufs, st);
+  const int dev = current_device();
+  if (p->graph_device >= 0 && p->graph_device != dev) p->release_graphs();
+  auto& e = p->graphs[k];
+  e.last = ++p->graph_clock;
+  if (!e.exec && ++e.calls >= 2) {
+    if (!p->capture_stream) {
+      cudaError_t ce = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking);
+      if (ce != cudaSuccess) {
+        p->capture_stream = nullptr;
+        return cuda_fail(ce, "creating the plan's capture stream");
+      }
+      p->graph_device = dev;
+    }
+    // at most kGraphCache instantiated graphs: drop the least recently used
+    constexpr size_t kGraphCache = 8;
+    size_t live = 0;
+    for (auto& kv : p->graphs) live += kv.second.exec != nullptr;
+    while (live >= kGraphCache) {
+      auto victim = p->graphs.end();
+      for (auto it = p->graphs.begin(); it != p->graphs.end(); ++it)
+        if (it->second.exec && (victim == p->graphs.end() || it->second.last < victim->second.last)) victim = it;
+      if (victim == p->graphs.end()) break;
+      cudaGraphExecDestroy(victim->second.exec);
+      victim->second.exec = nullptr;
+      victim->second.calls = 0;
+      --live;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeRelaxed);
+    int rc = TFFT_OK;
+    if (ce == cudaSuccess) {
+      rc = run_steps(p, steps, bufs, p->capture_stream);
+      ce = cudaStreamEndCapture(p->capture_stream, &g);
+    }
+    if (rc == TFFT_OK && ce == cudaSuccess && g) ce = cudaGraphInstantiate(&e.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc != TFFT_OK || ce != cudaSuccess || !e.exec) {
+      // the launches could not be captured: run them directly, now and later
+      cudaGetLastError();
+      e.exec = nullptr;
+      e.calls = -(1 << 30);
+      return run_steps(p, steps, bufs, st);
+    }
+  }
+  if (!e.exec) return run_steps(p, steps, bufs, st);
+  cudaError_t ce = cudaGraphLaunch(e.exec, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphLaunch");
+  return TFFT_OK;
 }
 
 }  // namespace host

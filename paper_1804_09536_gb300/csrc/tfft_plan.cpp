@@ -323,7 +323,7 @@ int tfft_plan_create(tfft_plan* plan, int ndims, const int64_t* shape, int grid_
     if (kind != TFFT_C2C && kind != TFFT_R2C) return fail(TFFT_EINVAL, "kind must be TFFT_C2C or TFFT_R2C");
     if (precision != TFFT_FP32 && precision != TFFT_TC_BF16X3 && precision != TFFT_TC_FP16X3)
       return fail(TFFT_EINVAL, "precision must be TFFT_FP32, TFFT_TC_BF16X3 or TFFT_TC_FP16X3");
-    if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA)) return fail(TFFT_EINVAL, "unknown flag bits");
+    if (flags & ~(TFFT_NORM_BACKWARD | TFFT_NO_TMA | TFFT_NO_GRAPH)) return fail(TFFT_EINVAL, "unknown flag bits");
     auto p = new tfft_plan_s();
     p->d = ndims;
     p->g = grid_ndims;
@@ -515,6 +515,7 @@ int tfft_plan_bind(tfft_plan p, void* d_state, size_t bytes, void* stream) {
     int rc = check_ptr(d_state, "d_state");
     if (rc) return rc;
     if (bytes < p->state_bytes) return fail(TFFT_EINVAL, "state buffer too small");
+    p->release_graphs();  // captured launches point into the previous state
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(d_state, p->image.data(), p->state_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (plan state)");

@@ -190,6 +190,46 @@ struct tfft_plan_s {
   char* d_state = nullptr;
   int device = -1;  // device the state was bound on
   std::vector<cudaEvent_t> events;
+  // Graphs of repeated executes: a call that repeats an earlier one (same
+  // direction, mode, buffers, device coefficient, factor and wait limit)
+  // replays the launches captured the second time they were requested (at
+  // most kGraphCache per plan, least recently used dropped).
+  struct GraphKey {
+    int key = 0, mode = 0;
+    const void* in = nullptr;
+    const void* out = nullptr;
+    const void* w0 = nullptr;
+    const void* w1 = nullptr;
+    const double* coef = nullptr;
+    double factor = 1.0;
+    uint32_t wait_limit = 0;
+    bool operator<(const GraphKey& o) const {
+      return std::tie(key, mode, in, out, w0, w1, coef, factor, wait_limit) <
+             std::tie(o.key, o.mode, o.in, o.out, o.w0, o.w1, o.coef, o.factor, o.wait_limit);
+    }
+  };
+  struct GraphEntry {
+    int calls = 0;
+    uint64_t last = 0;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::map<GraphKey, GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  int graph_device = -1;
+  cudaStream_t capture_stream = nullptr;  // private stream the launches are captured on
+  void release_graphs() {
+    if (graph_device < 0) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(graph_device);
+    for (auto& kv : graphs)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    cudaSetDevice(cur);
+    graphs.clear();
+    capture_stream = nullptr;
+    graph_device = -1;
+  }
   // copy streams and events of tfft_execute_host (created on first use)
   struct HostIo {
     int device = -1;
@@ -197,6 +237,7 @@ struct tfft_plan_s {
     cudaEvent_t in_done[2] = {}, comp_done[2] = {}, out_done[2] = {}, start = nullptr, end = nullptr;
   } io;
   ~tfft_plan_s() {
+    release_graphs();
     if (io.device < 0) return;
     int cur = 0;
     cudaGetDevice(&cur);
@@ -254,6 +295,8 @@ std::vector<Step> build_steps(tfft_plan p, int sign, int mode);
 void assign_buffers(std::vector<Step>& v, bool destroy_input);
 int launch_step(tfft_plan p, const Step& s, void* const* bufs, cudaStream_t st);
 int run_steps(tfft_plan p, const std::vector<Step>& steps, void* const* bufs, cudaStream_t st);
+int run_steps_cached(tfft_plan p, const tfft_plan_s::GraphKey& k, const std::vector<Step>& steps, void* const* bufs,
+                     cudaStream_t st);
 int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
                  size_t work_bytes, void* stream, const double* coef = nullptr, double factor = 1.0);
 

@@ -34,11 +34,13 @@ class Plan:
     Stage buffers are 1-D complex64 tensors holding every virtual rank's local
     array, concatenated in rank order.  ``forward`` maps stage 0 to stage g,
     ``inverse`` stage g to stage 0; ``redistribute(v, w)`` is the exchange of
-    Alg. 3 between the stages aligned in v and in w.
+    Alg. 3 between the stages aligned in v and in w.  ``graphs=False`` stops
+    ``execute`` from replaying the launches of repeated identical calls from a
+    CUDA graph (TFFT_NO_GRAPH).
     """
 
     def __init__(self, shape, grid, kind: str = "c2c", norm: str = "forward", device=None,
-                 bind: bool = True, tma: bool = True, precision: str = "fp32"):
+                 bind: bool = True, tma: bool = True, precision: str = "fp32", graphs: bool = True):
         self.shape = tuple(int(n) for n in shape)
         self.grid = tuple(int(m) for m in grid)
         self.kind = kind
@@ -46,6 +48,8 @@ class Plan:
         flags = {"forward": _lib.TFFT_NORM_FORWARD, "backward": _lib.TFFT_NORM_BACKWARD}[norm]
         if not tma:
             flags |= _lib.TFFT_NO_TMA
+        if not graphs:
+            flags |= _lib.TFFT_NO_GRAPH
         h = ctypes.c_void_p()
         shp = (ctypes.c_int64 * len(self.shape))(*self.shape)
         grd = (ctypes.c_int * max(1, len(self.grid)))(*(self.grid or (1,)))

@@ -254,3 +254,16 @@ def test_launch_bytes_account_for_every_pass(lib):
         if kind == "r2c":
             assert 8 * nc <= ws <= 8 * nc + 8 * nc // 16 + 64, (shape, grid, ws)
         checked += 1
+
+
+def test_plan_flags(lib):
+    """Known flag bits are accepted together; any other bit is rejected."""
+    from paper_1804_09536_gb300 import _lib
+    h = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 3)(16, 16, 16)
+    grd = (ctypes.c_int * 2)(2, 2)
+    every = _lib.TFFT_NORM_BACKWARD | _lib.TFFT_NO_TMA | _lib.TFFT_NO_GRAPH
+    assert lib.tfft_plan_create(ctypes.byref(h), 3, shp, 2, grd, _lib.TFFT_C2C, _lib.TFFT_FP32, every) == 0
+    lib.tfft_plan_destroy(h)
+    for bad in (1, 2, 32, 1 << 20):
+        assert lib.tfft_plan_create(ctypes.byref(h), 3, shp, 2, grd, _lib.TFFT_C2C, _lib.TFFT_FP32, bad) == 1

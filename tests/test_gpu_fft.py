@@ -488,3 +488,44 @@ def test_full_size_r2c_512_pencil_sampled(cuda_device):
     assert np.max(np.abs(got - want)) <= 1e-4 * rms
     back = p.inverse(y.clone())
     assert float(torch.linalg.vector_norm((back - b0).double()) / torch.linalg.vector_norm(b0.double())) <= RTOL_FP32
+
+
+@pytest.mark.parametrize("shape,grid,kind", [((32, 32, 32), (2, 2), "c2c"),
+                                             ((64, 128, 512), (4, 8), "r2c"),      # column window
+                                             ((512, 64, 100), (2, 3), "c2c")])     # rank groups, uneven
+def test_repeated_execute_replays_the_same_launches(cuda_device, shape, grid, kind):
+    """From the second identical call on, tfft_execute launches a CUDA graph of
+    its launches: every call's result equals the plan without graphs bit for
+    bit, also after the buffers or the wait limit change (new graphs), and
+    more distinct calls than the cache holds keep giving the same bits."""
+    from paper_1804_09536_gb300.plan import Plan
+    pg = Plan(shape, grid, kind=kind, device=cuda_device)
+    pn = Plan(shape, grid, kind=kind, device=cuda_device, graphs=False)
+    if kind == "r2c":
+        x = to_dev(R.scatter(inputs.normal_real(shape, seed=8).numpy(), grid, 0), cuda_device)
+    else:
+        x = to_dev(R.scatter(inputs.uniform_complex(shape, seed=8).numpy(), grid, 0), cuda_device)
+    ref = pn.forward(x)
+    refb = pn.inverse(ref.clone())
+    ys = [pg.empty_stage(pg.g) for _ in range(10)]
+    zs = [pg.empty_stage(0, real=kind == "r2c") for _ in range(2)]
+    w = pg.workspace("fused")
+    for rep in range(3):
+        for y in ys:                       # ten distinct keys: more than the cache keeps
+            y.fill_(float("nan"))
+            pg.execute(-1, x, y, "fused", w)
+        for z in zs:
+            yi = ys[0].clone() if kind == "r2c" else ys[0]
+            pg.execute(+1, yi, z, "fused", w)
+        torch.cuda.synchronize()
+        for y in ys:
+            assert torch.equal(y, ref), rep
+        for z in zs:
+            assert torch.equal(z, refb), rep
+    pg.set_wait_limit(1 << 20)             # a new key: captured again
+    for _ in range(3):
+        pg.execute(-1, x, ys[1], "fused", w)
+    pg.set_wait_limit(0)
+    torch.cuda.synchronize()
+    assert pg.device_status() == 0
+    assert torch.equal(ys[1], ref)
