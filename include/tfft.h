@@ -205,7 +205,8 @@ int tfft_partial(tfft_plan plan, int stage, int axis, int sign, void *inout, voi
  * and every later identical one launch the graph on `stream` instead -- the
  * same kernels with the same arguments, without the per-launch host cost
  * (a few microseconds per kernel).  The plan keeps at most 8 such graphs
- * (least recently used dropped) and destroys them with the plan; launch
+ * (least recently used dropped; the cache is locked, so several threads may
+ * execute one plan) and destroys them with the plan; launch
  * events (tfft_plan_set_launch_events) and TFFT_NO_GRAPH turn it off.  A
  * caller that frees a buffer and gets the same address back for a new one
  * simply replays the same launches on it.

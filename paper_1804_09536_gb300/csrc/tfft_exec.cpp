@@ -482,6 +482,7 @@ int run_steps_cached(tfft_plan p, const tfft_plan_s::GraphKey& k, const std::vec
     return run_steps(p, steps, bufs, st);
   }
   if (cs != cudaStreamCaptureStatusNone) return run_steps(p, steps, bufs, st);
+  std::lock_guard<std::mutex> lock(p->graph_mutex);
   const int dev = current_device();
   if (p->graph_device >= 0 && p->graph_device != dev) p->release_graphs();
   auto& e = p->graphs[k];

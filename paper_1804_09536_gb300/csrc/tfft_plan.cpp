@@ -515,7 +515,10 @@ int tfft_plan_bind(tfft_plan p, void* d_state, size_t bytes, void* stream) {
     int rc = check_ptr(d_state, "d_state");
     if (rc) return rc;
     if (bytes < p->state_bytes) return fail(TFFT_EINVAL, "state buffer too small");
-    p->release_graphs();  // captured launches point into the previous state
+    {
+      std::lock_guard<std::mutex> lock(p->graph_mutex);
+      p->release_graphs();  // captured launches point into the previous state
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemcpyAsync(d_state, p->image.data(), p->state_bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync (plan state)");

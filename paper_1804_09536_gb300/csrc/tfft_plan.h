@@ -15,6 +15,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <numeric>
@@ -214,6 +215,7 @@ struct tfft_plan_s {
     cudaGraphExec_t exec = nullptr;
   };
   std::map<GraphKey, GraphEntry> graphs;
+  std::mutex graph_mutex;  // calls on one plan from several threads share the cache
   uint64_t graph_clock = 0;
   int graph_device = -1;
   cudaStream_t capture_stream = nullptr;  // private stream the launches are captured on

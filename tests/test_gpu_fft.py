@@ -529,3 +529,40 @@ def test_repeated_execute_replays_the_same_launches(cuda_device, shape, grid, ki
     torch.cuda.synchronize()
     assert pg.device_status() == 0
     assert torch.equal(ys[1], ref)
+
+
+def test_execute_from_several_threads(cuda_device):
+    """One plan, four host threads, each with its own stream and output buffer,
+    calling tfft_execute repeatedly (the graph cache is shared and locked):
+    every output equals the single-threaded transform."""
+    import threading
+    from paper_1804_09536_gb300.plan import Plan
+    shape, grid = (64, 64, 128), (2, 4)
+    p = Plan(shape, grid, device=cuda_device)
+    x = to_dev(R.scatter(inputs.uniform_complex(shape, seed=12).numpy(), grid, 0), cuda_device)
+    ref = p.forward(x)
+    torch.cuda.synchronize()
+    outs = [[p.empty_stage(p.g) for _ in range(2)] for _ in range(4)]
+    works = [p.workspace("fused").clone() for _ in range(4)]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    errors = []
+
+    def run(t):
+        try:
+            with torch.cuda.device(cuda_device):
+                for it in range(6):
+                    p.execute(-1, x, outs[t][it % 2], "fused", works[t], stream=streams[t])
+                streams[t].synchronize()
+        except Exception as e:  # reported below
+            errors.append(e)
+    threads = [threading.Thread(target=run, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize()
+    assert not errors, errors
+    assert p.device_status() == 0
+    for t in range(4):
+        for y in outs[t]:
+            assert torch.equal(y, ref), t
