@@ -207,7 +207,9 @@ int tfft_partial(tfft_plan plan, int stage, int axis, int sign, void *inout, voi
  * (a few microseconds per kernel).  The plan keeps at most 8 such graphs
  * (least recently used dropped; the cache is locked, so several threads may
  * execute one plan) and destroys them with the plan; launch
- * events (tfft_plan_set_launch_events) and TFFT_NO_GRAPH turn it off.  A
+ * events (tfft_plan_set_launch_events) and TFFT_NO_GRAPH turn it off, and
+ * tfft_execute_host does not use it.  Instantiating a graph (the second
+ * identical call) may synchronise the device once.  A
  * caller that frees a buffer and gets the same address back for a new one
  * simply replays the same launches on it.
  */

@@ -394,7 +394,7 @@ int run_steps(tfft_plan p, const std::vector<Step>& steps, void* const* bufs, cu
 }
 
 int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
-                        size_t work_bytes, void* stream, const double* coef, double factor) {
+                        size_t work_bytes, void* stream, const double* coef, double factor, bool allow_graph) {
   if (!p) return fail(TFFT_EINVAL, "plan is NULL");
   if (int rcb = check_bound(p)) return rcb;
   if (sign != TFFT_FORWARD && sign != TFFT_BACKWARD) return fail(TFFT_EINVAL, "sign must be -1 or +1");
@@ -464,7 +464,7 @@ int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void*
     return fail(TFFT_EINVAL, "fewer launch events than launches + 1");
   void* bufs[4] = {const_cast<void*>(in), out, w0, w1};
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (!p->events.empty() || (p->flags & TFFT_NO_GRAPH)) return run_steps(p, steps, bufs, st);
+  if (!allow_graph || !p->events.empty() || (p->flags & TFFT_NO_GRAPH)) return run_steps(p, steps, bufs, st);
   return run_steps_cached(p, tfft_plan_s::GraphKey{key, mode, in, out, w0, w1, coef, factor, p->wait_limit}, steps,
                           bufs, st);
 }

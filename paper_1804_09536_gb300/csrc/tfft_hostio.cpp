@@ -99,7 +99,10 @@ int tfft_execute_host(tfft_plan p, int nsigns, const int* signs, int count, cons
       char* src = bin;
       for (int j = 0; j < nsigns; ++j) {
         char* dst = (j == nsigns - 1) ? bout : ((j % 2 == 0) ? bmid : bin);
-        rc = execute_impl(p, signs[j], signs[j], TFFT_MODE_FUSED, src, dst, bwork, B, stream);
+        // launched directly: instantiating a graph here could synchronise the
+        // device in the middle of the copy pipeline, and the copies bound it
+        rc = execute_impl(p, signs[j], signs[j], TFFT_MODE_FUSED, src, dst, bwork, B, stream, nullptr, 1.0,
+                          false);
         if (rc) return rc;
         src = dst;
       }

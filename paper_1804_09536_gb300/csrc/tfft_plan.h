@@ -300,7 +300,8 @@ int run_steps(tfft_plan p, const std::vector<Step>& steps, void* const* bufs, cu
 int run_steps_cached(tfft_plan p, const tfft_plan_s::GraphKey& k, const std::vector<Step>& steps, void* const* bufs,
                      cudaStream_t st);
 int execute_impl(tfft_plan p, int key, int sign, int mode, const void* in, void* out, void* work,
-                 size_t work_bytes, void* stream, const double* coef = nullptr, double factor = 1.0);
+                 size_t work_bytes, void* stream, const double* coef = nullptr, double factor = 1.0,
+                 bool allow_graph = true);
 
 // Runs an entry point's body so that no C++ exception (host allocation
 // failure, a library error) crosses the C ABI: it becomes an error status.
