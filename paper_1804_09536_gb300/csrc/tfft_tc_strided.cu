@@ -66,9 +66,13 @@ struct TcGeo {
   static constexpr uint32_t TMEM = NG * 32 < 32 ? 32 : (NG == 3 ? 128 : NG * 32);
   static constexpr size_t BUF = (size_t)L * W;  // complex elements per tile buffer
   static_assert(BUF * sizeof(float2) >= 2 * OP, "A fits in a tile buffer");
-  static constexpr size_t SMEM = 3 * BUF * sizeof(float2) + 2 * kBBytes + (L + L / 16) * sizeof(float2) +
-                                 5 * sizeof(uint64_t) + 2 * sizeof(uint32_t) + 2 * W * sizeof(float);
-  static constexpr int CTAS = SMEM <= 113 * 1024 ? 2 : 1;
+  // tile buffers: three (load i+1 / compute i / store i-1 drain) unless two
+  // let a third CTA fit on the SM
+  static constexpr size_t extra = 2 * kBBytes + (L + L / 16) * sizeof(float2) + 5 * sizeof(uint64_t) +
+                                  2 * sizeof(uint32_t) + 2 * W * sizeof(float);
+  static constexpr int NB = (2 * BUF * sizeof(float2) + extra <= 74 * 1024) ? 2 : 3;
+  static constexpr size_t SMEM = NB * BUF * sizeof(float2) + extra;
+  static constexpr int CTAS = SMEM <= 74 * 1024 ? 3 : (SMEM <= 113 * 1024 ? 2 : 1);
   static_assert(CTAS * TMEM <= 512, "tensor memory columns per SM");
 };
 
@@ -80,7 +84,8 @@ __global__ void __launch_bounds__(W * 16, TcGeo<L, E, W>::CTAS)
   constexpr int NT = G::NT, NW = NT / 32;
   constexpr int BUF = (int)G::BUF;
   extern __shared__ __align__(128) float2 smem[];
-  uint8_t* b_hi = reinterpret_cast<uint8_t*>(smem + 3 * BUF);
+  constexpr int NB = G::NB;
+  uint8_t* b_hi = reinterpret_cast<uint8_t*>(smem + NB * BUF);
   uint8_t* b_lo = b_hi + kBBytes;
   float2* s_tw = reinterpret_cast<float2*>(b_lo + kBBytes);
   uint64_t* bars = reinterpret_cast<uint64_t*>(s_tw + L + L / 16);  // [0..2] copies, [3] MMA
@@ -133,24 +138,26 @@ __global__ void __launch_bounds__(W * 16, TcGeo<L, E, W>::CTAS)
 
   int64_t tile = blockIdx.x;
   if (tid == 0 && tile < ntiles) issue_load(tile, smem, &bars[0]);
-  int it = 0, b = 0;  // b = it % 3
+  int it = 0, b = 0;  // b = it % NB
   uint32_t mma_phase = 0;
   bool mma_pending = false;  // an MMA group may still be running (failure path)
-  for (; tile < ntiles; tile += gridDim.x, ++it, b = (b == 2) ? 0 : b + 1) {
+  for (; tile < ntiles; tile += gridDim.x, ++it, b = (b == NB - 1) ? 0 : b + 1) {
     float2* cur = smem + b * BUF;
-    const int bn = (b == 2) ? 0 : b + 1;
+    const int bn = (b == NB - 1) ? 0 : b + 1;
     const int64_t next = tile + gridDim.x;
     if (tid == 0 && next < ntiles) {
-      bulk_wait_read<1>();  // the store of tile it-2 has finished reading buffer bn
+      // the store of tile it+1-NB has finished reading buffer bn
+      if constexpr (NB == 3) bulk_wait_read<1>();
+      else bulk_wait_read<0>();
       fence_proxy_async();
       issue_load(next, smem + bn * BUF, &bars[bn]);
     }
-    const bool ok = mbar_wait(&bars[b], (it / 3) & 1, a.wait_limit);
+    const bool ok = mbar_wait(&bars[b], (it / NB) & 1, a.wait_limit);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
-        mbar_wait(&bars[b], (it / 3) & 1, kWaitLimit);
-        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / 3) & 1, kWaitLimit);
+        mbar_wait(&bars[b], (it / NB) & 1, kWaitLimit);
+        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / NB) & 1, kWaitLimit);
       }
       break;
     }
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(W * 16, TcGeo<L, E, W>::CTAS)
       mma_pending = true;
       if (tid == 0) {
         atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
-        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / 3) & 1, kWaitLimit);
+        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / NB) & 1, kWaitLimit);
       }
       break;
     }
