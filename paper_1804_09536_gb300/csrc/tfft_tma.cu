@@ -40,9 +40,31 @@ namespace {
 using namespace tiles;
 using namespace tma;
 
-// Shared memory of the strided TMA kernel: three L x (W + 1) tile buffers.
+// CTAs of `bytes` of shared memory each that fit one SM's 228 KB (1 KB
+// reserved per CTA), at most three.
+__host__ __device__ constexpr int strided_tma_ctas(size_t bytes) {
+  return 228 * 1024 / (bytes + 1024) < 3 ? (int)(228 * 1024 / (bytes + 1024)) : 3;
+}
+
+// Tile buffers of the strided TMA kernel (L x (W + 1) each). Three let the
+// load of tile i+1 and the store of tile i-1 overlap the transform of tile i;
+// two make the load wait for the previous store to finish reading its buffer,
+// which pays where the smaller footprint adds a CTA per SM and either a lone
+// CTA would hold the SM (length 384: 0.202 -> 0.180 ms per 384^3 pass) or the
+// tile rows are 256 B wide (length 128, W = 32: 11.8 vs 12.2 us per 128^3
+// pass). With 128-byte rows (length 256, W = 16) the third CTA measured 1.5%
+// slower, so that one keeps three.
+__host__ __device__ constexpr int strided_tma_nbuf(int L, int W) {
+  return strided_tma_ctas(2 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t)) >
+                     strided_tma_ctas(3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t)) &&
+                 (strided_tma_ctas(3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t)) == 1 ||
+                  W * sizeof(float2) >= 256)
+             ? 2
+             : 3;
+}
+
 __host__ __device__ constexpr size_t strided_tma_smem(int L, int W) {
-  return 3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t);
+  return strided_tma_nbuf(L, W) * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t);
 }
 
 // Tiles of the equal-block view: (outer index, column block), gathered and
@@ -114,15 +136,17 @@ struct RankGroupTiles {
 };
 
 template <int L, int E, int W, class Geo, int... Rs>
-__global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1024 ? 2 : 1)
+__global__ void __launch_bounds__(W * (L / E), strided_tma_ctas(strided_tma_smem(L, W)))
     k_strided_tma(const StridedArgs a, const __grid_constant__ Geo geo) {
   constexpr int T = L / E, NST = sizeof...(Rs);
   constexpr int WP = (W % 16 == 0) ? W : W + 1;  // exchange pitch (bank-conflict padding)
   constexpr int BUF = L * (W + 1);
   extern __shared__ __align__(128) float2 smem[];
-  // three tile buffers: tile i is transformed in buffer i % 3 while tile i+1
-  // is loaded into the next one and the store of tile i-1 still reads its own
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 3 * BUF);
+  // NB tile buffers: tile i is transformed in buffer i % NB while tile i+1 is
+  // loaded into the next one; with three, the store of tile i-1 still reads
+  // its own meanwhile, with two it has finished before the load is issued
+  constexpr int NB = strided_tma_nbuf(L, W);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NB * BUF);
   const int cx = threadIdx.x;
   const int tid = threadIdx.y * W + cx;
   const bool inv = a.sign > 0;
@@ -130,7 +154,7 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
   const uint32_t tile_bytes = (uint32_t)(L * W * sizeof(float2));
 
   if (tid == 0) {
-    for (int b = 0; b < 3; ++b) mbar_init(&bars[b], 1);
+    for (int b = 0; b < NB; ++b) mbar_init(&bars[b], 1);
     fence_mbar_init();
     fence_proxy_async();
   }
@@ -145,25 +169,27 @@ __global__ void __launch_bounds__(W * (L / E), strided_tma_smem(L, W) <= 112 * 1
   if (tid == 0 && tile < ntiles) issue_load(tile, smem, &bars[0]);
   StageTwiddles<L, E, Rs...> twr;
   twr.load(threadIdx.y, a.tw);
-  int it = 0, b = 0;  // b = it % 3
-  for (; tile < ntiles; tile += gridDim.x, ++it, b = (b == 2) ? 0 : b + 1) {
+  int it = 0, b = 0;  // b = it % NB
+  for (; tile < ntiles; tile += gridDim.x, ++it, b = (b == NB - 1) ? 0 : b + 1) {
     float2* cur = smem + b * BUF;
-    const int bn = (b == 2) ? 0 : b + 1;
+    const int bn = (b == NB - 1) ? 0 : b + 1;
     const int64_t next = tile + gridDim.x;
     if (tid == 0 && next < ntiles) {
-      bulk_wait_read<1>();  // the store of tile it-2 has finished reading buffer bn
+      // the store of tile it+1-NB has finished reading buffer bn
+      if constexpr (NB == 3) bulk_wait_read<1>();
+      else bulk_wait_read<0>();
       fence_proxy_async();
       issue_load(next, smem + bn * BUF, &bars[bn]);
     }
     bool ok = true;
-    if (!mbar_wait(&bars[b], (it / 3) & 1, a.wait_limit)) ok = false;
+    if (!mbar_wait(&bars[b], (it / NB) & 1, a.wait_limit)) ok = false;
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(a.status, TFFT_DEVICE_ETIMEOUT);
         // give the copies still in flight (this tile's and the next one's) a
         // bounded chance to land before the CTA leaves
-        mbar_wait(&bars[b], (it / 3) & 1, kWaitLimit);
-        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / 3) & 1, kWaitLimit);
+        mbar_wait(&bars[b], (it / NB) & 1, kWaitLimit);
+        if (next < ntiles) mbar_wait(&bars[bn], ((it + 1) / NB) & 1, kWaitLimit);
       }
       break;
     }
