@@ -938,6 +938,36 @@ def batch48(dev, steps, barrier, autotune=True):
     with torch.cuda.graph(gp):
         per_plan()
     ms_plans_graph = timed(gp.replay)
+    # forward + inverse: a second batch (sign +1) reads the forward's outputs;
+    # each direction replayed from its own graph, and the same two directions
+    # plan by plan in one graph
+    bi = Batch(plans, sign=+1, ins=b.outs)
+    if autotune:
+        y_keep = [t.clone() for t in bi.ins]
+        bi.autotune(reps=3)
+        for t, k in zip(bi.ins, y_keep):
+            t.copy_(k)
+    gi = bi.graph()
+
+    def fwd_inv():
+        g.replay()
+        gi.replay()
+    ms_fi = timed(fwd_inv)
+    rt_num = sum(float((bi.outs[k] - x).abs().pow(2).sum()) for k, x in enumerate(b.ins))
+    rt_den = sum(float(x.abs().pow(2).sum()) for x in b.ins)
+
+    def per_plan_fi():
+        for k, p in enumerate(plans):
+            p.execute(-1, b.ins[k], b.outs[k], "fused", works[k])
+            p.execute(+1, b.outs[k], bi.outs[k], "fused", works[k])
+    with torch.cuda.stream(s):
+        per_plan_fi()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    gpi = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gpi):
+        per_plan_fi()
+    ms_plans_fi_graph = timed(gpi.replay)
     nsum = sum(math.prod(sh) for sh, _ in problems)
     flops = sum(5.0 * math.prod(sh) * math.log2(math.prod(sh)) for sh, _ in problems)
     nbytes = 3 * 16 * nsum
@@ -954,6 +984,15 @@ def batch48(dev, steps, barrier, autotune=True):
             "GFLOPs": round(flops / (ms_graph * 1e-3) / 1e9, 1),
             "hbm_frac": round(nbytes / (ms_graph * 1e-3) / 1e9 / peak, 4),
             "autotuned": bool(autotune),
+            "fwd_inv": {"graph_ms": round(ms_fi, 4), "executor": {"kind": bi.executor[0], "streams": bi.executor[1]},
+                        "per_plan_graph_ms": round(ms_plans_fi_graph, 4),
+                        "speedup_vs_per_plan_graph": round(ms_plans_fi_graph / ms_fi, 3),
+                        "GFLOPs": round(2 * flops / (ms_fi * 1e-3) / 1e9, 1),
+                        "hbm_frac": round(2 * nbytes / (ms_fi * 1e-3) / 1e9 / peak, 4),
+                        "round_trip_rel_l2": math.sqrt(rt_num / rt_den),
+                        "note": "forward batch then inverse batch (each its own graph, executor "
+                                "autotuned per direction); baseline: both directions plan by plan "
+                                "in one graph"},
             "variants": {f"{'contig' if k == 0 else 'strided'}_{L}": b.variant(k, L)
                          for k in (0, 1) for L in (64, 96, 128, 160, 256) if _has_variant(b, k, L)}}
 
