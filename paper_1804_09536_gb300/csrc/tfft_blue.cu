@@ -102,8 +102,12 @@ __host__ __device__ constexpr size_t blue_strided_smem(int N) {
          2 * (size_t)N * sizeof(uint32_t);
 }
 
+// Registers sized for 768 resident threads per SM (three 256-thread CTAs at
+// M = 256, a few bytes of spill): the pass is bound by instruction issue, and
+// the third CTA's warps raise it (512 x 127 x 512: 0.383 -> 0.334 ms per
+// pass); a 1024-thread target spills hundreds of bytes.
 template <int M, int E, int W, int... Rs>
-__global__ void __launch_bounds__(W * (M / E), min_blocks(E, W * (M / E), 512))
+__global__ void __launch_bounds__(W * (M / E), min_blocks(E, W * (M / E), 768))
     k_blue_strided_spec(const StridedArgs a, const BlueArgs b) {
   constexpr int T = M / E, NST = sizeof...(Rs);
   constexpr int R0 = radix_at<0, Rs...>(), RL = radix_at<NST - 1, Rs...>();
