@@ -32,8 +32,18 @@ __global__ void __launch_bounds__((L / E) * B, min_blocks(E, (L / E) * B, 1024))
 // CTA's lifetime (2L words): not at 4096, where it would halve the CTAs per SM.
 __host__ __device__ constexpr bool strided_cache_rows(int L) { return L <= 2048; }
 
+// Resident threads per SM the plain strided kernel's registers are sized
+// for: 1024 (min_blocks halves it for the plans of 20 or more values per
+// thread), and 1536 for the 20- and 24-value plans that fit 80 registers
+// without spilling (three 256-thread CTAs instead of two): 320^3 pass 0.166
+// -> 0.146 ms, 640 x 640 x 64 0.141 -> 0.136 ms.  The contiguous kernel gained
+// nothing from the same change (320^3 0.166 -> 0.165 ms, 160^3 slower).
+__host__ __device__ constexpr int strided_target(int L, int E) {
+  return E >= 20 && E < 32 && L != 384 && L != 480 ? 1536 : 1024;
+}
+
 template <int L, int E, int W, int... Rs>
-__global__ void __launch_bounds__(W * (L / E), min_blocks(E, W * (L / E), 1024))
+__global__ void __launch_bounds__(W * (L / E), min_blocks(E, W * (L / E), strided_target(L, E)))
     k_strided_spec(const StridedArgs a) {
   extern __shared__ float2 smem[];
   const int64_t ntiles = a.nouter * a.ncolblocks;
