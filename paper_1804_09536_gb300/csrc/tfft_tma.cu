@@ -49,16 +49,15 @@ __host__ __device__ constexpr int strided_tma_ctas(size_t bytes) {
 // Tile buffers of the strided TMA kernel (L x (W + 1) each). Three let the
 // load of tile i+1 and the store of tile i-1 overlap the transform of tile i;
 // two make the load wait for the previous store to finish reading its buffer,
-// which pays where the smaller footprint adds a CTA per SM and either a lone
-// CTA would hold the SM (length 384: 0.202 -> 0.180 ms per 384^3 pass) or the
-// tile rows are 256 B wide (length 128, W = 32: 11.8 vs 12.2 us per 128^3
-// pass). With 128-byte rows (length 256, W = 16) the third CTA measured 1.5%
-// slower, so that one keeps three.
+// which pays wherever the smaller footprint adds a CTA per SM: length 384
+// (one CTA -> two: 0.202 -> 0.180 ms per 384^3 pass), length 128 with 32
+// columns (12.2 -> 11.8 us per 128^3 pass), length 256 with 16 columns (the
+// batch of 48 1.881 -> 1.864 ms, the r2c slab's rank-group pass 22.9 -> 22.3
+// us; alone, a 256^3 pass 48.3 -> 49.4 us, 2 % slower, which the batch, where
+// these kernels share the GPU with others, more than wins back).
 __host__ __device__ constexpr int strided_tma_nbuf(int L, int W) {
   return strided_tma_ctas(2 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t)) >
-                     strided_tma_ctas(3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t)) &&
-                 (strided_tma_ctas(3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t)) == 1 ||
-                  W * sizeof(float2) >= 256)
+                 strided_tma_ctas(3 * (size_t)L * (W + 1) * sizeof(float2) + 3 * sizeof(uint64_t))
              ? 2
              : 3;
 }
