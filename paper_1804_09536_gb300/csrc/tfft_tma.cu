@@ -10,8 +10,9 @@
 // the line from its M owners (Alg. 3's subarray boxes) is done by the copy
 // engine -- and the result goes back the same way into the output stage,
 // whose box spans the other subgroup (the scatter).  Tiles are
-// buffered three deep: the copy of tile i+1 runs while tile i is
-// transformed and the store of tile i-1 drains.
+// buffered three deep -- the copy of tile i+1 runs while tile i is
+// transformed and the store of tile i-1 drains -- or two deep where the
+// smaller footprint lets one more CTA share the SM.
 //
 // The same kernel also runs in-place passes along the leading axis of layouts
 // whose ranks do NOT hold equal blocks (an uneven split of Eq. decompose):
