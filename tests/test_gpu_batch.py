@@ -248,3 +248,29 @@ def test_stream_executor_without_workspaces(cuda_device, sign):
     assert b.device_status() == 0
     for k in range(len(probs)):
         assert torch.equal(b.outs[k], refs[k]), k
+
+
+def test_forward_batch_feeds_inverse_batch(cuda_device):
+    """A backward batch built over the forward batch's output buffers (the
+    forward + inverse step of the batch workload): both replay from their own
+    graphs, each equals the plans' own transforms bit for bit, and the round
+    trip returns the input (paper normalisation: 1/N on the forward)."""
+    from paper_1804_09536_gb300.plan import Batch
+    plans = _plans(SMALL, cuda_device)
+    fwd = Batch(plans, sign=-1)
+    for k, (shape, grid) in enumerate(SMALL):
+        fwd.ins[k].copy_(to_dev(R.scatter(inputs.uniform_complex(shape, seed=600 + k).numpy(), grid, 0), cuda_device))
+    inv = Batch(plans, sign=+1, ins=fwd.outs)
+    assert all(a.data_ptr() == b.data_ptr() for a, b in zip(inv.ins, fwd.outs))
+    gf, gi = fwd.graph(), inv.graph()
+    for _ in range(2):
+        gf.replay()
+        gi.replay()
+    torch.cuda.synchronize()
+    assert fwd.device_status() == 0 and inv.device_status() == 0
+    for k, p in enumerate(plans):
+        y = p.forward(fwd.ins[k])
+        assert torch.equal(fwd.outs[k], y), k
+        assert torch.equal(inv.outs[k], p.inverse(y)), k
+        err = rel_l2(inv.outs[k].cpu().numpy(), fwd.ins[k].cpu().numpy())
+        assert err <= RTOL_FP32, (k, err)
